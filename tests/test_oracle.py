@@ -1,0 +1,363 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Every test here runs without a GPU.  Each pin checks the oracle against something
+other than itself: a library routine, a closed form, an invariant, brute force or
+a value the paper prints (tests/golden/).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from gen import problems as G
+from oracle import chase_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Jacobi eig
+
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 16, 33])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_jacobi_matches_lapack(k, cplx):
+    g = np.random.default_rng(k + 100 * cplx)
+    X = g.standard_normal((k, k)) + (1j * g.standard_normal((k, k)) if cplx else 0)
+    H = 0.5 * (X + np.conj(X.T))
+    w, Z = O.jacobi_eigh(H)
+    wl = np.linalg.eigvalsh(H)
+    nrm = np.linalg.norm(H, 2)
+    assert np.max(np.abs(w - wl)) <= 1e-13 * nrm
+    assert np.max(np.abs(np.conj(Z.T) @ Z - np.eye(k))) <= 1e-13
+    assert np.max(np.abs(H @ Z - Z * w)) <= 1e-13 * nrm
+    assert np.all(np.diff(w) >= 0)
+
+
+def test_jacobi_closed_form_121():
+    n = 40
+    w, _ = O.jacobi_eigh(G.matrix_121(n))
+    assert np.max(np.abs(w - G.spectrum_121(n))) <= 1e-14 * 4
+
+
+def test_jacobi_wilkinson_vs_sturm():
+    for n in (21, 20):
+        W = G.matrix_wilkinson(n)
+        w, _ = O.jacobi_eigh(W)
+        ws = O.tridiag_bisection(np.diag(W).copy(), np.ones(n - 1))
+        assert np.max(np.abs(w - ws)) <= 1e-12 * np.max(np.abs(ws))
+        assert np.sum(w < 0) == 1  # Table 1: all positive but one
+
+
+def test_jacobi_degenerate_cluster():
+    # exactly repeated eigenvalues: any orthonormal basis of the eigenspace is valid
+    g = np.random.default_rng(7)
+    Qm, _ = np.linalg.qr(g.standard_normal((12, 12)) + 1j * g.standard_normal((12, 12)))
+    lam = np.array([-1.0] * 4 + [0.5] * 5 + [2.0] * 3)
+    H = Qm @ np.diag(lam) @ np.conj(Qm.T)
+    H = 0.5 * (H + np.conj(H.T))
+    w, Z = O.jacobi_eigh(H)
+    assert np.max(np.abs(w - lam)) <= 1e-13 * 2
+    assert np.max(np.abs(H @ Z - Z * w)) <= 1e-13 * 2
+
+
+# ---------------------------------------------------------------- paper-printed condition numbers
+
+def _sturm_kth(d, e, j):
+    r = np.max(np.abs(d)) + 2.0
+    lo, hi = -r, r
+    for _ in range(100):
+        mid = 0.5 * (lo + hi)
+        if O.sturm_count(d, e, mid) > j:
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+def test_condition_numbers_printed_in_paper():
+    gold = json.load(open(os.path.join(GOLDEN, "condition_numbers_20k.json")))
+    n = gold["n"]
+    sig = gold["significant_digits"]
+
+    def same(x, y):
+        return float(f"{x:.{sig - 1}e}") == float(f"{y:.{sig - 1}e}")
+
+    lam = G.spectrum_121(n)
+    assert same(lam[-1] / lam[0], gold["kappa"]["1-2-1"])
+    for name, fn in (("Uniform", G.spectrum_uniform_table1), ("Geometric", G.spectrum_geometric_table1)):
+        lam = fn(n)
+        assert same(np.max(np.abs(lam)) / np.min(np.abs(lam)), gold["kappa"][name])
+    d = G.wilkinson_diagonal(n)
+    e = np.ones(n - 1)
+    neg = O.sturm_count(d, e, 0.0)
+    assert neg == gold["wilkinson_negative_eigenvalues"]
+    lmax = _sturm_kth(d, e, n - 1)
+    small = min(abs(_sturm_kth(d, e, neg - 1)), abs(_sturm_kth(d, e, neg)))
+    assert same(lmax / small, gold["kappa"]["Wilkinson"])
+
+
+# ---------------------------------------------------------------- generators
+
+def test_dense_generator_matches_prescribed_spectrum_and_wy():
+    p = G.problem_small(48, 4, 4, complex_=True, k_reflect=5)
+    A = p.dense()
+    assert np.allclose(A, np.conj(A.T), atol=0)
+    assert np.max(np.abs(np.linalg.eigvalsh(A) - p.lam)) <= 1e-13
+    E = G.exact_eigvecs(p.U, np.arange(48))
+    assert np.max(np.abs(np.conj(E.T) @ E - np.eye(48))) <= 1e-13
+    assert np.max(np.abs(A @ E - E * p.lam)) <= 1e-13
+    x = p.V0[:, :3]
+    assert np.max(np.abs(G.implicit_matvec(p.lam, p.U, x) - A @ x)) <= 1e-13
+    B, D = G.wy_factors(p.lam, p.U)
+    n = p.n
+    Aw = np.diag(p.lam).astype(complex) - (B @ np.conj(p.U.T)) * p.lam[None, :] \
+        - p.lam[:, None] * (p.U @ np.conj(B.T)) + D @ np.conj(B.T)
+    assert np.max(np.abs(Aw - A)) <= 1e-13
+
+
+# ---------------------------------------------------------------- QR
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_householder_qr_invariants(cplx):
+    g = np.random.default_rng(3)
+    X = g.standard_normal((80, 12)) + (1j * g.standard_normal((80, 12)) if cplx else 0)
+    Q, R = O.householder_qr(X)
+    assert np.max(np.abs(np.conj(Q.T) @ Q - np.eye(12))) <= 1e-14 * 12
+    assert np.linalg.norm(Q @ R - X) <= 1e-14 * np.linalg.norm(X)
+    Ql, _ = np.linalg.qr(X)
+    # same span as LAPACK's QR
+    s = np.linalg.svd(np.conj(Ql.T) @ Q, compute_uv=False)
+    assert np.min(s) >= 1 - 1e-13
+
+
+def test_qr_step_restores_locked():
+    g = np.random.default_rng(4)
+    Y, _ = np.linalg.qr(g.standard_normal((50, 3)) + 1j * g.standard_normal((50, 3)))
+    V = g.standard_normal((50, 5)) + 1j * g.standard_normal((50, 5))
+    Q = O.qr_step(Y, V)
+    assert np.array_equal(Q[:, :3], Y)
+    assert np.max(np.abs(np.conj(Q.T) @ Q - np.eye(8))) <= 1e-13
+
+
+# ---------------------------------------------------------------- filter
+
+def test_filter_coefficients_reproduce_scaled_chebyshev():
+    b_sup, mu_1, mu_ne = 3.0, -2.0, 0.5
+    c, e, al, be = O.filter_coefficients(b_sup, mu_1, mu_ne, 30)
+    x = np.linspace(-2.5, 3.0, 41)
+    y_prev = np.ones_like(x)
+    y = al[1] * (x - c) * y_prev
+    for s in range(2, 31):
+        y, y_prev = al[s] * (x - c) * y + be[s] * y_prev, y
+        ref = O.chebyshev_scalar(x, s, b_sup, mu_1, mu_ne)
+        assert np.max(np.abs(y - ref) / np.maximum(1, np.abs(ref))) <= 1e-12
+    # normalisation: p_m(mu_1) = 1
+    assert abs(O.chebyshev_scalar(np.array([mu_1]), 17, b_sup, mu_1, mu_ne)[0] - 1.0) <= 1e-14
+
+
+def test_filter_on_exact_eigenvectors():
+    p = G.problem_small(60, 4, 4, complex_=True)
+    A = p.dense()
+    idx = np.array([0, 3, 7, 20, 45, 59])
+    E = G.exact_eigvecs(p.U, idx)
+    m = np.array([1, 2, 5, 9, 13, 20])
+    b_sup, mu_1, mu_ne = 1.1, -0.95, -0.6
+    out, mv = O.chebyshev_filter(A, E, m, b_sup, mu_1, mu_ne)
+    assert mv == m.sum()
+    for a in range(idx.size):
+        pm = O.chebyshev_scalar(np.array([p.lam[idx[a]]]), int(m[a]), b_sup, mu_1, mu_ne)[0]
+        assert np.linalg.norm(out[:, a] - pm * E[:, a]) <= 1e-12 * max(1.0, abs(pm))
+
+
+def test_filter_degree_zero_columns_independent():
+    # a column's result depends only on its own degree, not on the others
+    p = G.problem_small(40, 4, 4, complex_=False)
+    A = p.dense()
+    V = p.V0[:, :4]
+    m = np.array([3, 3, 8, 11])
+    out, _ = O.chebyshev_filter(A, V, m, 1.2, -1.0, -0.3)
+    for a in range(4):
+        single, _ = O.chebyshev_filter(A, V[:, a:a + 1], m[a:a + 1], 1.2, -1.0, -0.3)
+        assert np.allclose(single[:, 0], out[:, a], rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- Lanczos
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_lanczos_bounds_bracket_spectrum(cplx):
+    p = G.problem_small(300, 10, 6, complex_=cplx, seed_pid=2)
+    A = p.dense()
+    lz = O.lanczos_bounds(A, p.L0, 25, p.ne)
+    assert lz.b_sup >= p.lam[-1]
+    assert lz.mu_1 >= p.lam[0] - 1e-12
+    assert lz.mu_1 <= p.lam[0] + 0.05 * (p.lam[-1] - p.lam[0])
+    assert lz.mu_1 < lz.mu_ne < lz.b_sup
+    # DoS estimate of the ne-th eigenvalue lies in the lower part of the spectrum
+    assert lz.mu_ne <= p.lam[0] + 0.5 * (p.lam[-1] - p.lam[0])
+    # tau^2 of each run sums to one (spectral measure of a unit start vector)
+    for t2 in lz.tau2:
+        assert abs(np.sum(t2) - 1.0) <= 1e-12
+
+
+def test_lanczos_tridiagonal_exact_on_small_matrix():
+    # n steps of Lanczos on an n x n matrix reproduce its full spectrum
+    p = G.problem_small(12, 2, 2, complex_=True)
+    A = p.dense()
+    lz = O.lanczos_bounds(A, p.L0[:, :1], 12, 4)
+    assert np.max(np.abs(lz.thetas[0] - p.lam)) <= 1e-12
+
+
+# ---------------------------------------------------------------- residuals, degrees, locking
+
+def test_residuals_and_lock():
+    p = G.problem_small(30, 3, 3, complex_=True)
+    A = p.dense()
+    E = G.exact_eigvecs(p.U, [0, 1, 2])
+    r = O.residuals(A, E, p.lam[:3])
+    assert np.max(r) <= 1e-13
+    assert O.lock_prefix(np.array([1e-12, 1e-11, 1.0, 1e-15]), 1e-10) == 2
+    assert O.lock_prefix(np.array([1.0, 1e-15]), 1e-10) == 0
+
+
+def test_degrees_properties():
+    c, e = 10.0, 9.0        # damped interval [1, 19]
+    w = np.array([-5.0, -5.0, -1.0, 0.999, 1.0])
+    res = np.array([1e-2, 1e-6, 1e-2, 1e-2, 1e-2])
+    m = O.degrees(res, w, 1e-10, c, e, 36)
+    assert m[0] > m[1]                  # smaller residual -> lower degree
+    assert m[2] >= m[0]                 # closer to the interval -> higher degree
+    assert m[4] == 36                   # on the interval edge
+    assert np.all((m >= 1) & (m <= 36))
+    # converged residual -> minimum degree range
+    assert O.degrees(np.array([1e-12]), np.array([-5.0]), 1e-10, c, e, 36)[0] <= 2
+    # explicit value: rho = |t| + sqrt(t^2 - 1)
+    t = (-5.0 - c) / e
+    rho = abs(t) + np.sqrt(t * t - 1)
+    assert m[0] == int(np.ceil(np.log(1e-2 / 1e-10) / np.log(rho))) + 2
+
+
+def test_sort_by_degree_stable():
+    m = np.array([5, 3, 5, 3, 7])
+    w = np.array([0.1, 0.5, -0.2, 0.4, 0.0])
+    order = O.sort_by_degree(m, w)
+    assert list(order) == [3, 1, 2, 0, 4]
+
+
+# ---------------------------------------------------------------- full solve
+
+@pytest.mark.parametrize("cplx,n,nev,nex", [(True, 40, 4, 4), (False, 64, 6, 6), (True, 96, 8, 4)])
+def test_solve_brute_force_small(cplx, n, nev, nex):
+    p = G.problem_small(n, nev, nex, complex_=cplx, seed_pid=n)
+    A = p.dense()
+    r = O.chase_solve(A, nev, nex, 1e-10, 20, 36, p.V0, p.L0, 25)
+    assert r.converged
+    wl = np.linalg.eigvalsh(A)[:nev]
+    nrm = np.max(np.abs(p.lam))
+    assert np.max(np.abs(r.eigvals - wl)) <= 1e-10 * nrm
+    res = O.residuals(A, r.eigvecs, r.eigvals)
+    assert np.max(res) <= 1e-10 * nrm * 1.0000001
+    assert np.max(np.abs(np.conj(r.eigvecs.T) @ r.eigvecs - np.eye(nev))) <= 1e-12
+
+
+def test_solve_c1_prescribed_spectrum():
+    p = G.problem_c1()
+    A = p.dense()
+    r = O.chase_solve(A, p.nev, p.nex, p.tol, p.deg, p.maxdeg, p.V0, p.L0, p.lanczos_steps)
+    assert r.converged
+    nrm = p.norm2()
+    assert np.max(np.abs(r.eigvals - p.lam[:p.nev])) <= 1e-10 * nrm
+    # exact residuals through the implicit operator Q diag(lam) Q^H
+    R = G.implicit_matvec(p.lam, p.U, r.eigvecs) - r.eigvecs * r.eigvals[None, :]
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.0000001
+    # subspace angle vs exact Q e_i within the Davis-Kahan bound tol*||A|| / gap
+    E = G.exact_eigvecs(p.U, np.arange(p.nev))
+    s = np.linalg.svd(np.conj(E.T) @ r.eigvecs, compute_uv=False)
+    angle = np.sqrt(max(0.0, 1 - np.min(s) ** 2))
+    gap = p.lam[p.nev] - p.lam[p.nev - 1]
+    assert angle <= 2.0 * p.tol * nrm / gap
+    assert r.matvecs > 0 and r.iterations >= 2
+
+
+def test_solve_121_closed_form():
+    n = 200
+    A = G.matrix_121(n)
+    p = G.from_dense("121", A, 8, 6)
+    r = O.chase_solve(A, 8, 6, 1e-10, 20, 36, p.V0, p.L0, 25)
+    assert r.converged
+    assert np.max(np.abs(r.eigvals - G.spectrum_121(n)[:8])) <= 1e-10 * 4
+
+
+def test_planted_sign_error_in_filter_is_caught(monkeypatch):
+    # a plausible mistake (wrong sign of the three-term beta) must fail the closed-form pin
+    orig = O.filter_coefficients
+
+    def wrong(b_sup, mu_1, mu_ne, mmax):
+        c, e, al, be = orig(b_sup, mu_1, mu_ne, mmax)
+        return c, e, al, -be
+
+    monkeypatch.setattr(O, "filter_coefficients", wrong)
+    p = G.problem_small(60, 4, 4, complex_=True)
+    A = p.dense()
+    E = G.exact_eigvecs(p.U, [0])
+    out, _ = O.chebyshev_filter(A, E, np.array([6]), 1.1, -0.95, -0.6)
+    pm = O.chebyshev_scalar(np.array([p.lam[0]]), 6, 1.1, -0.95, -0.6)[0]
+    assert np.linalg.norm(out[:, 0] - pm * E[:, 0]) > 1e-6
+
+
+# ---------------------------------------------------------------- backward
+
+def _loss_parts(A, nev, w, B):
+    lam, V = np.linalg.eigh(A)
+    lam, V = lam[:nev], V[:, :nev]
+    M = V.T @ B @ V
+    L = float(w @ lam + np.sum(M * M))
+    gV = 4.0 * B @ V @ M
+    return L, lam, V, gV
+
+
+def test_backward_dense_vs_finite_differences():
+    n, nev = 30, 4
+    g = np.random.default_rng(11)
+    lam = G.spectrum_gapped(g, n, nlow=nev + 2, gap=5e-2)
+    U = g.standard_normal((n, 4))
+    A = G.dense_A(lam, U)
+    w = g.standard_normal(nev)
+    Bm = g.standard_normal((n, n))
+    Bm = 0.5 * (Bm + Bm.T)
+    L, lam_c, V, gV = _loss_parts(A, nev, w, Bm)
+    Ab = O.eig_backward_dense(A, w, gV, nev)
+    h = 1e-6
+    for t in range(4):
+        D = g.standard_normal((n, n))
+        D = 0.5 * (D + D.T)
+        Lp = _loss_parts(A + h * D, nev, w, Bm)[0]
+        Lm = _loss_parts(A - h * D, nev, w, Bm)[0]
+        fd = (Lp - Lm) / (2 * h)
+        an = float(np.sum(Ab * D))
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+def test_backward_minres_matches_dense():
+    n, nev = 50, 5
+    g = np.random.default_rng(12)
+    lam = G.spectrum_gapped(g, n, nlow=nev + 2, gap=2e-2)
+    A = G.dense_A(lam, g.standard_normal((n, 3)))
+    w = g.standard_normal(nev)
+    Bm = g.standard_normal((n, n))
+    Bm = 0.5 * (Bm + Bm.T)
+    _, lam_c, V, gV = _loss_parts(A, nev, w, Bm)
+    Ab_alg = O.eig_backward(A, lam_c, V, w, gV, minres_tol=1e-13)
+    Ab_ref = O.eig_backward_dense(A, w, gV, nev)
+    assert np.max(np.abs(Ab_alg - Ab_ref)) <= 1e-9 * np.max(np.abs(Ab_ref))
+
+
+def test_backward_eigenvalue_only_is_v_diag_vt():
+    n, nev = 25, 3
+    g = np.random.default_rng(13)
+    lam = G.spectrum_gapped(g, n, nlow=nev + 1, gap=5e-2)
+    A = G.dense_A(lam, g.standard_normal((n, 3)))
+    lam_c, V = np.linalg.eigh(A)
+    lam_c, V = lam_c[:nev], V[:, :nev]
+    w = g.standard_normal(nev)
+    Ab = O.eig_backward(A, lam_c, V, w, np.zeros((n, nev)))
+    assert np.max(np.abs(Ab - V @ np.diag(w) @ V.T)) <= 1e-14
