@@ -1,0 +1,183 @@
+/*
+ * chase_gb300.h -- C ABI of a single-GPU (GB300, sm_103a) Chebyshev-accelerated
+ * subspace iteration eigensolver (ChASE, Algorithm 1 of the paper).
+ *
+ * Problem (Section "Distributed eigensolvers", Eq. AV = V Lambda): the nev
+ * lowest eigenpairs of a dense n x n complex Hermitian or real symmetric A.
+ *
+ * Conventions for every entry point
+ *   - Matrices are column-major with an explicit leading dimension (elements).
+ *     Complex matrices are interleaved (re, im) doubles (C99 double complex /
+ *     cuDoubleComplex / torch.complex128 layout); real ones are doubles.
+ *   - Pointers named *_dev are device pointers on the context's device; the
+ *     caller owns them and they must stay valid for the duration of the call.
+ *     Pointers named *_host are host pointers.
+ *   - All work is enqueued on the context's stream.  Calls that return results
+ *     to the host synchronise that stream; the others are asynchronous unless
+ *     stated.
+ *   - Every call returns a chase_status.  Nothing throws across the ABI.  On a
+ *     non-OK status chase_last_error() holds a one-line description.  An
+ *     asynchronous device error surfaces as CHASE_ERR_CUDA at the next call.
+ *   - A is read-only: the Chebyshev shift (A - cI) is fused into the product
+ *     epilogue and never applied to A in place (the paper shifts in place).
+ */
+#ifndef CHASE_GB300_H
+#define CHASE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chase_ctx chase_ctx;
+
+typedef enum {
+  CHASE_OK = 0,
+  CHASE_ERR_ARG = 1,          /* invalid argument (sizes, null pointer, mode) */
+  CHASE_ERR_OOM = 2,          /* workspace does not fit in device memory */
+  CHASE_ERR_NOCONV = 3,       /* maxiter outer iterations without locking nev pairs */
+  CHASE_ERR_QR_BREAKDOWN = 4, /* Cholesky-QR failed even after the shifted fallback */
+  CHASE_ERR_NAN = 5,          /* a NaN/Inf appeared (e.g. in A or the start block) */
+  CHASE_ERR_CUDA = 6,         /* a CUDA runtime/driver error */
+  CHASE_ERR_STATE = 7,        /* call out of order (e.g. eigvals before solve) */
+  CHASE_ERR_TIMEOUT = 8,      /* a bounded device-side loop hit its iteration cap */
+  CHASE_ERR_UNSUPPORTED = 9   /* mode not available on this device */
+} chase_status;
+
+typedef enum { CHASE_R64 = 0, CHASE_C128 = 1 } chase_dtype;
+
+/* Arithmetic of the Chebyshev filter products (Algorithm 1, line 4).
+ * QR, Rayleigh-Ritz, the small eigensolve, residuals and Lanczos always run with
+ * FP64 accuracy. */
+typedef enum {
+  CHASE_FP64 = 0,       /* FP64-accurate products: split-BF16 tensor-core products
+                           with exact FP32 partial sums, combined in integer/FP64 */
+  CHASE_FP64_NATIVE = 1,/* plain DFMA kernels (reference path; slow on this chip) */
+  CHASE_BF16x3 = 2,     /* mixed: 2-slice split-BF16 (3 products) bulk filter, then
+                           FP64 sweeps once residuals reach the bulk precision */
+  CHASE_BF16x6 = 3      /* mixed: 3-slice split-BF16 (6 products) bulk filter */
+} chase_mode;
+
+typedef struct {
+  int maxdeg;          /* largest filter degree per vector (default 36) */
+  int lanczos_steps;   /* Lanczos steps per run (default 25) */
+  int lanczos_runs;    /* independent Lanczos runs (default 4) */
+  int maxiter;         /* outer iterations before CHASE_ERR_NOCONV (default 30) */
+  int extra_deg;       /* constant added to the optimised degree (default 2) */
+  int nfinal;          /* mixed modes: minimum FP64 sweeps at the end (default 1) */
+  int oz_slices;       /* FP64 mode: BF16 slices per operand (default 6) */
+} chase_opts;
+
+typedef struct {
+  int iterations;      /* outer iterations of Algorithm 1 */
+  int locked;          /* converged (locked) pairs */
+  int64_t matvecs;     /* filter matrix-vector products: sum of degrees (footnote on Matvecs) */
+  int64_t matvecs_lowp;/* of which were done in the mixed-precision bulk mode */
+  int lowp_iterations; /* outer iterations that used the mixed-precision filter */
+  double ms_total, ms_lanczos, ms_filter, ms_qr, ms_rr, ms_resid;  /* stage times (CUDA events) */
+  double b_sup, mu_1, mu_ne, norm_est;   /* spectral bounds after Lanczos */
+  double max_resid;    /* largest relative residual among the returned pairs */
+  int qr_fallbacks;    /* shifted Cholesky-QR fallbacks taken */
+  int filter_launches; /* filter product launches */
+} chase_stats_t;
+
+/* Fill *opts with defaults. */
+void chase_default_opts(chase_opts* opts);
+
+/* Create a context on the current CUDA device.  Preallocates the whole
+ * workspace for problems up to n_max x n_max with nev+nex <= ne_max (the
+ * single-GPU form of Eq. GPU_mem plus split-product buffers); returns
+ * CHASE_ERR_OOM early if it does not fit.  stream: a cudaStream_t or NULL for
+ * a new non-blocking stream owned by the context.  opts may be NULL. */
+chase_status chase_create(chase_ctx** ctx, int64_t n_max, int ne_max, chase_dtype dtype,
+                          const chase_opts* opts, void* stream);
+void chase_destroy(chase_ctx* ctx);
+const char* chase_last_error(const chase_ctx* ctx);
+
+/* Device memory the context would allocate for (n_max, ne_max, dtype, mode set),
+ * in bytes; the single-GPU form of Eq. GPU_mem (n^2 term excluded: A is the
+ * caller's) plus split-product buffers. */
+int64_t chase_workspace_bytes(int64_t n_max, int ne_max, chase_dtype dtype, const chase_opts* opts);
+
+/* Algorithm 1 end to end.  A_dev: n x n Hermitian (lda >= n).  V0_dev: optional
+ * n x (nev+nex) start block (ld n); NULL is an error in this build: the caller
+ * supplies the random block.  L0_dev: n x lanczos_runs Lanczos start vectors (ld n).
+ * Converged when the residual of each of the nev lowest Ritz pairs is
+ * <= tol * ||A||_est (||A||_est: largest Lanczos Ritz value magnitude).
+ * Synchronous: returns when the solve has finished. */
+chase_status chase_solve(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, int nev, int nex,
+                         double tol, int deg, int mode, const void* V0_dev, const void* L0_dev);
+
+/* Batched / warm-start form: nprob independent problems solved one after the
+ * other with the same context (sizes <= the context's), each from its own start
+ * block (warm start: pass the previous step's eigenvectors padded to nev+nex).
+ * Eigenpairs are written to the caller's arrays: eigvals_dev[p] (nev[p] doubles),
+ * eigvecs_dev[p] (n[p] x (nev[p]+nex[p]), ld n[p]; on exit the leading nev[p]
+ * columns are the eigenvectors and the rest the next start block). */
+chase_status chase_solve_batched(chase_ctx* ctx, int nprob, const void* const* A_dev, const int64_t* n,
+                                 const int* nev, const int* nex, double tol, int deg, int mode,
+                                 void* const* V_dev, const void* const* L0_dev, double* const* eigvals_dev,
+                                 chase_stats_t* stats_host);
+
+/* Results of the last solve: nev eigenvalues ascending; eigenvectors n x nev. */
+chase_status chase_eigvals(chase_ctx* ctx, double* out, int on_device);
+chase_status chase_eigvecs(chase_ctx* ctx, void* out, int64_t ldv, int on_device);
+chase_status chase_stats(const chase_ctx* ctx, chase_stats_t* out);
+
+/* Adjoint of (Lambda, V) = the last solve's eigenpairs, real symmetric only.
+ * gbar_lambda_dev: nev doubles or NULL; gbar_V_dev: n x nev (ld ldg) or NULL;
+ * gbar_A_dev: n x n output (ld ldga), symmetrised.  A_dev must be the matrix of
+ * the last solve.  Abar = V (diag(gl) + F o (V^T Vbar)) V^T + X V^T with
+ * F_ij = 1/(lambda_j - lambda_i) and X from projected MINRES on (A - lambda_j I). */
+chase_status chase_backward(chase_ctx* ctx, const void* A_dev, int64_t lda, const double* gbar_lambda_dev,
+                            const void* gbar_V_dev, int64_t ldg, void* gbar_A_dev, int64_t ldga,
+                            double minres_tol, int minres_maxit);
+
+/* ---------------------------------------------------------------------------
+ * Step-level entry points (one step of Algorithm 1 each), used for per-step
+ * parity checks and by advanced callers.  All device buffers are the caller's.
+ * ------------------------------------------------------------------------- */
+
+/* Algorithm 1, line 2: Lanczos bounds.  out_host[0..3] = {b_sup, mu_1, mu_ne, theta_max}. */
+chase_status chase_lanczos(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, int ne,
+                           const void* L0_dev, int runs, int steps, double* out_host);
+
+/* Algorithm 1, line 4: filter ncols columns of V in place (ld ldv) with degrees
+ * deg_host[a] (non-decreasing) using the scaled three-term recurrence with
+ * c = (b_sup+mu_ne)/2, e = (b_sup-mu_ne)/2.  mode: a chase_mode. */
+chase_status chase_filter(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, void* V_dev, int64_t ldv,
+                          int ncols, const int* deg_host, double b_sup, double mu_1, double mu_ne, int mode);
+
+/* Algorithm 1, line 5: orthonormalise X (n x ncols, ld ldx) in place by
+ * Cholesky-QR2 (shifted Cholesky-QR3 fallback); the first nlocked columns are
+ * assumed orthonormal and are left unchanged. */
+chase_status chase_qr(chase_ctx* ctx, void* X_dev, int64_t n, int64_t ldx, int ncols, int nlocked);
+
+/* Algorithm 1, lines 6-7: Rayleigh-Ritz on the ncols orthonormal columns Q
+ * (in place: on exit the Ritz vectors), Ritz values ascending to ritz_host and
+ * residual norms ||A v - lambda v||_2 to resid_host. */
+chase_status chase_rayleigh_ritz(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, void* Q_dev,
+                                 int64_t ldq, int ncols, double* ritz_host, double* resid_host);
+
+/* Dense Hermitian eigensolve of G (k x k, ld ldg) on the device by parallel
+ * cyclic Jacobi: eigenvalues ascending to w_host, eigenvectors to Z_dev (ld ldz). */
+chase_status chase_heevj(chase_ctx* ctx, const void* G_dev, int64_t ldg, int k, double* w_host,
+                         void* Z_dev, int64_t ldz);
+
+/* Dense product C = A B (n x n times n x ncols) with the filter's product
+ * arithmetic for the given mode; used to check the split-product kernels. */
+chase_status chase_hemm(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, const void* B_dev,
+                        int64_t ldb, int ncols, void* C_dev, int64_t ldc, int mode);
+
+/* Input generator (not part of Algorithm 1): A = Q diag(lam) Q^H with Q a
+ * product of k Householder reflectors, from the compact-WY factors U, B = U T
+ * and D = B (U^H diag(lam) U) (each n x k, ld n, host-computed).  Writes an
+ * exactly Hermitian A (ld lda). */
+chase_status chase_generate(chase_ctx* ctx, void* A_dev, int64_t n, int64_t lda, const double* lam_dev,
+                            const void* U_dev, const void* B_dev, const void* D_dev, int k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHASE_GB300_H */

@@ -1,0 +1,7 @@
+"""GB300-native (sm_103a) Chebyshev-accelerated subspace iteration (ChASE) on one GPU.
+
+The compute path is the shared library libchase_gb300.so (C ABI in
+include/chase_gb300.h); this package only marshals arguments to it.
+"""
+from .api import Chase, colmajor, workspace_bytes  # noqa: F401
+from ._lib import MODES, ChaseError, load  # noqa: F401

@@ -1,0 +1,471 @@
+// FP64 (DFMA) dense kernels: tiled GEMM with a fused epilogue and split-K,
+// column reductions, column permutations, blocked Cholesky and right TRSM.
+//
+// These are the FP64-exact building blocks of Algorithm 1 (QR via Cholesky-QR,
+// Rayleigh-Ritz projection and back-transform, residual norms) and the
+// reference path of the Chebyshev filter product.  On GB300 FP64 runs on the
+// CUDA cores only (about 1.2 TFLOP/s), so the large products of the
+// production path go through the split-BF16 tensor-core kernels instead.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace chase {
+
+// ============================================================== GEMM
+constexpr int GB_M = 64, GB_N = 64;
+
+template <typename T> struct GK { static constexpr int BK = 8; };
+template <> struct GK<double> { static constexpr int BK = 16; };
+
+template <typename T>
+__device__ inline void epi_store(const Epi& e, int64_t i, int64_t j, T acc) {
+  using s = S<T>;
+  T v = s::scale(acc, e.alpha);
+  if (e.Y) {
+    double g = e.gamma * (e.ycol ? e.ycol[j] : 1.0);
+    v = s::add(v, s::scale(((const T*)e.Y)[i + j * e.ldy], g));
+  }
+  if (e.Z) v = s::add(v, s::scale(((const T*)e.Z)[i + j * e.ldz], e.beta));
+  ((T*)e.C)[i + j * e.ldc] = v;
+}
+
+template <typename T, int OPA, int OPB>
+__global__ void __launch_bounds__(256) gemm_f64_kernel(int64_t M, int64_t N, int64_t K, const T* __restrict__ A,
+                                                       int64_t lda, const T* __restrict__ B, int64_t ldb, Epi epi,
+                                                       T* __restrict__ work, int64_t kchunk) {
+  using s = S<T>;
+  constexpr int BK = GK<T>::BK;
+  __shared__ T As[BK][GB_M + 1];
+  __shared__ T Bs[BK][GB_N + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int64_t m0 = (int64_t)blockIdx.x * GB_M, n0 = (int64_t)blockIdx.y * GB_N;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk;
+  const int64_t ke = min(K, kb + kchunk);
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = s::zero();
+
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+    // A tile: BM x BK
+#pragma unroll
+    for (int t = tid; t < GB_M * BK; t += 256) {
+      int i, kk;
+      if (OPA == OP_N) { i = t % GB_M; kk = t / GB_M; } else { kk = t % BK; i = t / BK; }
+      int64_t gi = m0 + i, gk = k0 + kk;
+      T v = s::zero();
+      if (gi < M && gk < ke) v = (OPA == OP_N) ? A[gi + gk * lda] : s::conj(A[gk + gi * lda]);
+      As[kk][i] = v;
+    }
+#pragma unroll
+    for (int t = tid; t < GB_N * BK; t += 256) {
+      int j, kk;
+      if (OPB == OP_N) { kk = t % BK; j = t / BK; } else { j = t % GB_N; kk = t / GB_N; }
+      int64_t gj = n0 + j, gk = k0 + kk;
+      T v = s::zero();
+      if (gj < N && gk < ke) v = (OPB == OP_N) ? B[gk + gj * ldb] : s::conj(B[gj + gk * ldb]);
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = s::fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int64_t i = m0 + ty + 16 * r, j = n0 + tx + 16 * c;
+      if (i < M && j < N) {
+        if (work)
+          work[(int64_t)blockIdx.z * M * N + i + j * M] = acc[r][c];
+        else
+          epi_store<T>(epi, i, j, acc[r][c]);
+      }
+    }
+}
+
+template <typename T>
+__global__ void splitk_reduce_kernel(int64_t M, int64_t N, int nsplit, const T* __restrict__ work, Epi epi) {
+  using s = S<T>;
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  T acc = s::zero();
+  for (int z = 0; z < nsplit; ++z) acc = s::add(acc, work[(int64_t)z * M * N + idx]);
+  epi_store<T>(epi, idx % M, idx / M, acc);
+}
+
+template <typename T>
+void gemm_f64(cudaStream_t st, Op opA, Op opB, int64_t M, int64_t N, int64_t K, const T* A, int64_t lda, const T* B,
+              int64_t ldb, const Epi& epi, T* work, int64_t work_elems) {
+  if (M <= 0 || N <= 0) return;
+  constexpr int BK = GK<T>::BK;
+  int64_t tiles = (int64_t)ceil_div(M, GB_M) * ceil_div(N, GB_N);
+  int nsplit = 1;
+  if (K > 0) {
+    int64_t want = (2 * 152 + tiles - 1) / tiles;  // aim for >= 2 waves of blocks
+    int64_t maxsplit = K / (8 * BK);
+    nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(maxsplit, 64)));
+    if (work == nullptr || work_elems < nsplit * M * N) nsplit = 1;
+  }
+  int64_t kchunk = K > 0 ? ((K + nsplit - 1) / nsplit + BK - 1) / BK * BK : BK;
+  if (K <= 0) {
+    // C = epilogue with acc = 0
+    nsplit = 1;
+  }
+  dim3 grid(ceil_div(M, GB_M), ceil_div(N, GB_N), nsplit);
+  T* w = nsplit > 1 ? work : nullptr;
+#define LAUNCH(OA, OB) gemm_f64_kernel<T, OA, OB><<<grid, 256, 0, st>>>(M, N, std::max<int64_t>(K, 0), A, lda, B, ldb, epi, w, kchunk)
+  if (opA == OP_N && opB == OP_N) LAUNCH(OP_N, OP_N);
+  else if (opA == OP_C && opB == OP_N) LAUNCH(OP_C, OP_N);
+  else if (opA == OP_N && opB == OP_C) LAUNCH(OP_N, OP_C);
+  else LAUNCH(OP_C, OP_C);
+#undef LAUNCH
+  CHASE_CHECK_LAUNCH();
+  if (nsplit > 1) {
+    splitk_reduce_kernel<T><<<ceil_div(M * N, 256), 256, 0, st>>>(M, N, nsplit, work, epi);
+    CHASE_CHECK_LAUNCH();
+  }
+}
+
+// ============================================================== column reductions
+template <typename T>
+__global__ void colnorms_kernel(int64_t n, const T* __restrict__ X, int64_t ldx, double* out) {
+  using s = S<T>;
+  const T* x = X + (int64_t)blockIdx.x * ldx;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += s::abs2(x[i]);
+  __shared__ double red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[blockIdx.x] = sqrt(v);
+  }
+}
+
+template <typename T> void colnorms(cudaStream_t st, int64_t n, int k, const T* X, int64_t ldx, double* out) {
+  if (k <= 0) return;
+  colnorms_kernel<T><<<k, 256, 0, st>>>(n, X, ldx, out);
+  CHASE_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void colmaxabs_kernel(int64_t n, const T* __restrict__ X, int64_t ldx, double* out) {
+  using s = S<T>;
+  const T* x = X + (int64_t)blockIdx.x * ldx;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    T v = x[i];
+    m = fmax(m, fmax(fabs(s::re(v)), fabs(s::im(v))));
+  }
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
+}
+
+template <typename T> void colmaxabs(cudaStream_t st, int64_t n, int k, const T* X, int64_t ldx, double* out) {
+  if (k <= 0) return;
+  colmaxabs_kernel<T><<<k, 256, 0, st>>>(n, X, ldx, out);
+  CHASE_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void fro_partial_kernel(int64_t n, int k, const T* __restrict__ X, int64_t ldx, double* out) {
+  // one block per column: sum |x|^2 ; then summed in column order by a single thread
+  using s = S<T>;
+  const T* x = X + (int64_t)blockIdx.x * ldx;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += s::abs2(x[i]);
+  __shared__ double red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
+}
+
+__global__ void sum_kernel(int k, const double* in, double* out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < k; i += 32) acc += in[i];
+  acc = warp_sum(acc);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+template <typename T> void fro_norm2(cudaStream_t st, int64_t n, int k, const T* X, int64_t ldx, double* out) {
+  // out[0] = ||X||_F^2 ; out[1..k] scratch
+  fro_partial_kernel<T><<<k, 256, 0, st>>>(n, k, X, ldx, out + 1);
+  CHASE_CHECK_LAUNCH();
+  sum_kernel<<<1, 32, 0, st>>>(k, out + 1, out);
+  CHASE_CHECK_LAUNCH();
+}
+
+// ============================================================== column moves
+template <typename T>
+__global__ void permute_cols_kernel(int64_t n, const T* __restrict__ src, int64_t lds, T* __restrict__ dst,
+                                    int64_t ldd, const int* __restrict__ perm) {
+  int a = blockIdx.y;
+  int p = perm ? perm[a] : a;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i + a * ldd] = src[i + p * lds];
+}
+
+template <typename T>
+void permute_cols(cudaStream_t st, int64_t n, int k, const T* src, int64_t lds, T* dst, int64_t ldd, const int* perm) {
+  if (k <= 0 || n <= 0) return;
+  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 64), k);
+  permute_cols_kernel<T><<<grid, 256, 0, st>>>(n, src, lds, dst, ldd, perm);
+  CHASE_CHECK_LAUNCH();
+}
+
+template <typename T>
+void copy_cols(cudaStream_t st, int64_t n, int k, const T* src, int64_t lds, T* dst, int64_t ldd) {
+  if (k <= 0 || n <= 0) return;
+  CHASE_CUDA(cudaMemcpy2DAsync(dst, ldd * sizeof(T), src, lds * sizeof(T), n * sizeof(T), k,
+                               cudaMemcpyDeviceToDevice, st));
+}
+
+template <typename T>
+__global__ void scale_cols_kernel(int64_t n, T* X, int64_t ldx, const double* s, int invert) {
+  int a = blockIdx.y;
+  double f = s[a];
+  if (invert) f = (f > 0.0) ? 1.0 / f : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    X[i + a * ldx] = S<T>::scale(X[i + a * ldx], f);
+}
+
+template <typename T> void scale_cols(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const double* s, int invert) {
+  if (k <= 0 || n <= 0) return;
+  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 64), k);
+  scale_cols_kernel<T><<<grid, 256, 0, st>>>(n, X, ldx, s, invert);
+  CHASE_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void add_diag_kernel(int k, T* G, int64_t ldg, const double* shift_dev, double shift) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  double sh = shift + (shift_dev ? *shift_dev : 0.0);
+  T v = G[i + i * ldg];
+  G[i + i * ldg] = S<T>::make(S<T>::re(v) + sh, 0.0);
+}
+
+template <typename T> void add_diag(cudaStream_t st, int k, T* G, int64_t ldg, const double* shift_dev, double shift) {
+  add_diag_kernel<T><<<ceil_div(k, 256), 256, 0, st>>>(k, G, ldg, shift_dev, shift);
+  CHASE_CHECK_LAUNCH();
+}
+
+template <typename T> __global__ void hermitianize_kernel(int k, T* G, int64_t ldg) {
+  int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= k || j >= k || i < j) return;
+  using s = S<T>;
+  if (i == j) {
+    G[i + i * ldg] = s::make(s::re(G[i + i * ldg]), 0.0);
+    return;
+  }
+  T a = G[i + j * ldg], b = s::conj(G[j + i * ldg]);
+  T m = s::scale(s::add(a, b), 0.5);
+  G[i + j * ldg] = m;
+  G[j + i * ldg] = s::conj(m);
+}
+
+template <typename T> void hermitianize(cudaStream_t st, int k, T* G, int64_t ldg) {
+  dim3 grid(ceil_div(k, 32), ceil_div(k, 32));
+  hermitianize_kernel<T><<<grid, dim3(32, 32), 0, st>>>(k, G, ldg);
+  CHASE_CHECK_LAUNCH();
+}
+
+// ============================================================== Cholesky and TRSM
+constexpr int CB = 32;  // block size of the blocked Cholesky / TRSM
+
+// Unblocked Cholesky of one CB x CB diagonal block in shared memory (lower).
+template <typename T> __global__ void potrf_diag_kernel(int nb, T* G, int64_t ldg, int* info, int col0) {
+  using s = S<T>;
+  __shared__ T a[CB][CB + 1];
+  __shared__ int bad;
+  int i = threadIdx.x, j = threadIdx.y;  // element (i, j)
+  if (i == 0 && j == 0) bad = 0;
+  if (i < nb && j < nb) a[i][j] = G[i + j * ldg];
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (i == c && j == c) {
+      double d = s::re(a[c][c]);
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        d = 1.0;
+      }
+      a[c][c] = s::make(sqrt(d), 0.0);
+    }
+    __syncthreads();
+    double piv = s::re(a[c][c]);
+    if (j == c && i > c && i < nb) a[i][c] = s::scale(a[i][c], 1.0 / piv);
+    __syncthreads();
+    if (i > c && j > c && i < nb && j <= i) a[i][j] = s::sub(a[i][j], s::mul(a[i][c], s::conj(a[j][c])));
+    __syncthreads();
+  }
+  if (i < nb && j < nb) G[i + j * ldg] = (j <= i) ? a[i][j] : s::zero();
+  if (i == 0 && j == 0 && bad && info) atomicMax(info, col0 + 1);
+}
+
+// X(rows x nb) <- X L^{-H} with L the nb x nb lower block (row-parallel forward substitution).
+template <typename T>
+__global__ void trsm_rows_kernel(int64_t rows, int nb, T* X, int64_t ldx, const T* L, int64_t ldl) {
+  using s = S<T>;
+  __shared__ T l[CB][CB + 1];
+  for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
+    int i = t % CB, j = t / CB;
+    l[i][j] = (i < nb && j < nb && j <= i) ? L[i + j * ldl] : s::zero();
+  }
+  __syncthreads();
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  T q[CB];
+#pragma unroll
+  for (int j = 0; j < CB; ++j) {
+    if (j < nb) {
+      T v = X[r + j * ldx];
+#pragma unroll
+      for (int m = 0; m < CB; ++m)
+        if (m < j) v = s::sub(v, s::mul(q[m], s::conj(l[j][m])));
+      q[j] = s::scale(v, 1.0 / s::re(l[j][j]));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < CB; ++j)
+    if (j < nb) X[r + j * ldx] = q[j];
+}
+
+template <typename T>
+void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems) {
+  for (int j0 = 0; j0 < k; j0 += CB) {
+    int nb = std::min(CB, k - j0);
+    T* Gjj = G + j0 + (int64_t)j0 * ldg;
+    potrf_diag_kernel<T><<<1, dim3(CB, CB), 0, st>>>(nb, Gjj, ldg, info, j0);
+    CHASE_CHECK_LAUNCH();
+    int rest = k - j0 - nb;
+    if (rest <= 0) break;
+    T* P = G + (j0 + nb) + (int64_t)j0 * ldg;  // panel below the diagonal block
+    trsm_rows_kernel<T><<<ceil_div(rest, 128), 128, 0, st>>>(rest, nb, P, ldg, Gjj, ldg);
+    CHASE_CHECK_LAUNCH();
+    // trailing update  G22 -= P P^H
+    T* G22 = G + (j0 + nb) + (int64_t)(j0 + nb) * ldg;
+    Epi e;
+    e.C = G22;
+    e.ldc = ldg;
+    e.alpha = -1.0;
+    e.Z = G22;
+    e.ldz = ldg;
+    e.beta = 1.0;
+    gemm_f64<T>(st, OP_N, OP_C, rest, rest, nb, P, ldg, P, ldg, e, work, work_elems);
+  }
+}
+
+template <typename T>
+void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T* L, int64_t ldl, T* work,
+                   int64_t work_elems) {
+  for (int j0 = 0; j0 < k; j0 += CB) {
+    int nb = std::min(CB, k - j0);
+    T* Xb = X + (int64_t)j0 * ldx;
+    const T* Ljj = L + j0 + (int64_t)j0 * ldl;
+    trsm_rows_kernel<T><<<ceil_div(n, 128), 128, 0, st>>>(n, nb, Xb, ldx, Ljj, ldl);
+    CHASE_CHECK_LAUNCH();
+    int rest = k - j0 - nb;
+    if (rest <= 0) break;
+    // X[:, j0+nb:] -= Xb * L[j0+nb:, j0:j0+nb]^H
+    T* Xr = X + (int64_t)(j0 + nb) * ldx;
+    Epi e;
+    e.C = Xr;
+    e.ldc = ldx;
+    e.alpha = -1.0;
+    e.Z = Xr;
+    e.ldz = ldx;
+    e.beta = 1.0;
+    gemm_f64<T>(st, OP_N, OP_C, n, rest, nb, Xb, ldx, L + (j0 + nb) + (int64_t)j0 * ldl, ldl, e, work, work_elems);
+  }
+}
+
+// ============================================================== generator
+template <typename T>
+__global__ void generate_wy_kernel(T* A, int64_t n, int64_t lda, const double* __restrict__ lam,
+                                   const T* __restrict__ U, const T* __restrict__ B, const T* __restrict__ D, int k) {
+  // A_ij = lam_i d_ij - lam_j sum_a B_ia conj(U_ja) - lam_i sum_a U_ia conj(B_ja) + sum_a D_ia conj(B_ja)
+  // computed for i >= j and mirrored so A is exactly Hermitian.
+  using s = S<T>;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t j = (int64_t)blockIdx.y;
+  if (i >= n || i < j) return;
+  T t1 = s::zero(), t2 = s::zero(), t3 = s::zero();
+  for (int a = 0; a < k; ++a) {
+    T bja = B[j + a * n];
+    t1 = s::fma(B[i + a * n], s::conj(U[j + a * n]), t1);
+    t2 = s::fma(U[i + a * n], s::conj(bja), t2);
+    t3 = s::fma(D[i + a * n], s::conj(bja), t3);
+  }
+  T v = s::sub(s::sub(t3, s::scale(t1, lam[j])), s::scale(t2, lam[i]));
+  if (i == j) {
+    A[i + i * lda] = s::make(s::re(v) + lam[i], 0.0);
+  } else {
+    A[i + j * lda] = v;
+    A[j + i * lda] = s::conj(v);
+  }
+}
+
+template <typename T>
+void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* lam, const T* U, const T* B, const T* D,
+                 int k) {
+  // grid.y = columns (<= 2^31-1 OK for n up to 65535 per launch dimension limit): split if needed
+  for (int64_t j0 = 0; j0 < n; j0 += 65535) {
+    int64_t nj = std::min<int64_t>(65535, n - j0);
+    (void)nj;
+  }
+  CHASE_REQUIRE(n <= 65535, 1, "generator supports n <= 65535");
+  dim3 grid(ceil_div(n, 256), n);
+  generate_wy_kernel<T><<<grid, 256, 0, st>>>(A, n, lda, lam, U, B, D, k);
+  CHASE_CHECK_LAUNCH();
+}
+
+// ============================================================== instantiations
+#define INST(T)                                                                                                   \
+  template void gemm_f64<T>(cudaStream_t, Op, Op, int64_t, int64_t, int64_t, const T*, int64_t, const T*, int64_t, \
+                            const Epi&, T*, int64_t);                                                            \
+  template void colnorms<T>(cudaStream_t, int64_t, int, const T*, int64_t, double*);                              \
+  template void colmaxabs<T>(cudaStream_t, int64_t, int, const T*, int64_t, double*);                             \
+  template void fro_norm2<T>(cudaStream_t, int64_t, int, const T*, int64_t, double*);                             \
+  template void permute_cols<T>(cudaStream_t, int64_t, int, const T*, int64_t, T*, int64_t, const int*);          \
+  template void copy_cols<T>(cudaStream_t, int64_t, int, const T*, int64_t, T*, int64_t);                         \
+  template void scale_cols<T>(cudaStream_t, int64_t, int, T*, int64_t, const double*, int);                       \
+  template void add_diag<T>(cudaStream_t, int, T*, int64_t, const double*, double);                               \
+  template void hermitianize<T>(cudaStream_t, int, T*, int64_t);                                                  \
+  template void potrf_lower<T>(cudaStream_t, int, T*, int64_t, int*, T*, int64_t);                                \
+  template void trsm_right_lh<T>(cudaStream_t, int64_t, int, T*, int64_t, const T*, int64_t, T*, int64_t);        \
+  template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int);
+INST(double)
+INST(double2)
+#undef INST
+
+}  // namespace chase

@@ -1,0 +1,826 @@
+// ChASE driver (Algorithm 1) on one GPU and the C ABI declared in
+// include/chase_gb300.h.
+//
+// Device-resident loop: the start block, the locked prefix and the active
+// block share one n x ne buffer V (locked columns [0, l), active [l, ne)); two
+// more n x ne buffers hold the filter's ping-pong partner / Ritz vectors (T1)
+// and A Q (T2).  Per outer iteration the host reads one small status record
+// (locked count, degrees, bounds) to size the next filter launches; nothing
+// else crosses the host-device boundary (the paper does one transfer per
+// iteration too, Section "Offloading Selected Routines to GPUs").
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/chase_gb300.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "oz.h"
+
+using namespace chase;
+
+struct chase_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  chase_dtype dtype = CHASE_C128;
+  chase_opts opts{};
+  int64_t n_max = 0;
+  int ne_max = 0;
+  size_t esz = 16;  // scalar size
+  // workspace
+  void* V = nullptr;
+  void* T1 = nullptr;
+  void* T2 = nullptr;
+  void* G = nullptr;
+  void* Z = nullptr;
+  void* work = nullptr;
+  int64_t work_elems = 0;
+  double* dwork = nullptr;
+  int64_t dwork_elems = 0;
+  int* iwork = nullptr;
+  double* ritz = nullptr;
+  double* res = nullptr;
+  double* ritz2 = nullptr;
+  double* res2 = nullptr;
+  double* lam_locked = nullptr;
+  double* bounds = nullptr;
+  double* eigvals = nullptr;
+  int* deg = nullptr;
+  int* perm = nullptr;
+  int* info = nullptr;
+  int* status_dev = nullptr;
+  oz::Workspace ozw{};
+  // result state
+  bool have_result = false;
+  int64_t n = 0;
+  int nev = 0, nex = 0;
+  chase_stats_t stats{};
+  std::string err;
+  cudaEvent_t ev[8] = {};
+};
+
+namespace {
+
+struct Timer {
+  cudaStream_t st;
+  cudaEvent_t a, b;
+  double* acc;
+  Timer(chase_ctx* c, int slot, double* acc_) : st(c->stream), a(c->ev[2 * slot]), b(c->ev[2 * slot + 1]), acc(acc_) {
+    CHASE_CUDA(cudaEventRecord(a, st));
+  }
+  void stop() {
+    CHASE_CUDA(cudaEventRecord(b, st));
+    CHASE_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CHASE_CUDA(cudaEventElapsedTime(&ms, a, b));
+    *acc += ms;
+  }
+};
+
+void filter_coeffs(double b_sup, double mu_1, double mu_ne, int mmax, double& c, double& e, std::vector<double>& al,
+                   std::vector<double>& be) {
+  // Scaled three-term recurrence (Eq. three-terms-recurrence) with gamma = c:
+  // Y_1 = (sigma_1/e)(A - cI)Y_0, Y_{s+1} = (2 sigma_{s+1}/e)(A - cI)Y_s - sigma_s sigma_{s+1} Y_{s-1},
+  // sigma_1 = e/(mu_1 - c), sigma_{s+1} = 1/(2/sigma_1 - sigma_s).
+  c = 0.5 * (b_sup + mu_ne);
+  e = 0.5 * (b_sup - mu_ne);
+  double sigma1 = e / (mu_1 - c);
+  al.assign(mmax + 1, 0.0);
+  be.assign(mmax + 1, 0.0);
+  double sigma = sigma1;
+  if (mmax >= 1) al[1] = sigma1 / e;
+  for (int s = 1; s < mmax; ++s) {
+    double sn = 1.0 / (2.0 / sigma1 - sigma);
+    al[s + 1] = 2.0 * sn / e;
+    be[s + 1] = -sigma * sn;
+    sigma = sn;
+  }
+}
+
+template <typename T> __global__ void gather_odd_kernel(int64_t n, const int* deg, T* V, int64_t ldv, const T* Y1, int64_t ldy) {
+  int a = blockIdx.y;
+  if ((deg[a] & 1) == 0) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    V[i + a * ldv] = Y1[i + a * ldy];
+}
+
+__global__ void fill_int_kernel(int n, int* x, int v) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = v;
+}
+
+__global__ void init_bounds_kernel(const double* lz4, double* bounds) {
+  bounds[0] = lz4[0];
+  bounds[1] = lz4[1];
+  bounds[2] = lz4[2];
+  bounds[3] = 0.5 * (lz4[0] + lz4[2]);
+  bounds[4] = 0.5 * (lz4[0] - lz4[2]);
+  bounds[5] = 1e308;
+}
+
+__global__ void nan_check_kernel(int64_t n, int k, const double* X, int64_t ldx, int* flag) {
+  // X viewed as doubles: n rows (already scaled by scalar width) x k columns
+  int a = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(X[i + a * ldx])) atomicOr(flag, 1);
+}
+
+// rank-sort the l locked eigenvalues, output first nev ascending and the permutation
+__global__ void final_sort_kernel(int l, int nev, const double* lam, double* out, int* perm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= l) return;
+  double wi = lam[i];
+  int rank = 0;
+  for (int j = 0; j < l; ++j) rank += (lam[j] < wi) || (lam[j] == wi && j < i);
+  perm[rank] = i;
+  if (rank < nev) out[rank] = wi;
+}
+
+// MINRES helpers for the adjoint (real symmetric) ------------------------------------------
+struct MinresScalars {
+  double beta1, beta, oldb, dbar, epsln, phibar, cs, sn, alfa, phi, gamma, delta, oldeps, shift;
+  int active;
+};
+
+}  // namespace
+
+// =====================================================================================
+template <typename T> struct Solver {
+  chase_ctx* c;
+  explicit Solver(chase_ctx* ctx) : c(ctx) {}
+  T* V() { return (T*)c->V; }
+  T* T1() { return (T*)c->T1; }
+  T* T2() { return (T*)c->T2; }
+  T* Gb() { return (T*)c->G; }
+  T* Zb() { return (T*)c->Z; }
+  T* W() { return (T*)c->work; }
+  cudaStream_t st() { return c->stream; }
+
+  void check_nan(const T* X, int64_t n, int k, int64_t ld, const char* what) {
+    CHASE_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), st()));
+    int64_t rows = n * (int64_t)(sizeof(T) / sizeof(double));
+    dim3 grid(std::min<unsigned>(ceil_div(rows, 256), 64), k);
+    nan_check_kernel<<<grid, 256, 0, st()>>>(rows, k, (const double*)X, ld * (int64_t)(sizeof(T) / sizeof(double)),
+                                             c->status_dev);
+    CHASE_CHECK_LAUNCH();
+    int flag = 0;
+    CHASE_CUDA(cudaMemcpyAsync(&flag, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st()));
+    CHASE_CUDA(cudaStreamSynchronize(st()));
+    CHASE_REQUIRE(flag == 0, CHASE_ERR_NAN, std::string("non-finite values in ") + what);
+  }
+
+  // C(n x k) = A(n x n) * B(n x k) with epilogue, in the given filter arithmetic.
+  void hemm(const T* A, int64_t n, int64_t lda, const T* B, int64_t ldb, int k, const Epi& e, int mode) {
+    if (mode == CHASE_FP64_NATIVE || !oz::available()) {
+      gemm_f64<T>(st(), OP_N, OP_N, n, k, n, A, lda, B, ldb, e, W(), c->work_elems);
+    } else {
+      oz::hemm<T>(st(), c->ozw, A, n, lda, B, ldb, k, e, mode);
+    }
+  }
+
+  // ------------------------------------------------------------ Algorithm 1, line 4
+  // Filter the k columns of Y0 (ld n) in place; T1 (ld n) is the ping-pong partner.
+  // deg_host non-decreasing; deg_dev the same on the device.
+  int64_t filter(const T* A, int64_t n, int64_t lda, T* Y0, T* Y1, int k, const int* deg_host, const int* deg_dev,
+                 double b_sup, double mu_1, double mu_ne, int mode) {
+    if (k <= 0) return 0;
+    int mmax = deg_host[k - 1];
+    double cc, ee;
+    std::vector<double> al, be;
+    filter_coeffs(b_sup, mu_1, mu_ne, mmax, cc, ee, al, be);
+    if (mode != CHASE_FP64_NATIVE && oz::available()) oz::prepare_A<T>(st(), c->ozw, A, n, lda, mode);
+    T* B[2] = {Y0, Y1};
+    int f = 0;
+    int64_t mv = 0;
+    for (int s = 1; s <= mmax; ++s) {
+      while (f < k && deg_host[f] < s) ++f;
+      int cols = k - f;
+      if (cols <= 0) break;
+      mv += cols;
+      T* out = B[s & 1] + (int64_t)f * n;
+      const T* in = B[(s - 1) & 1] + (int64_t)f * n;
+      Epi e;
+      e.C = out;
+      e.ldc = n;
+      e.alpha = al[s];
+      e.Y = in;
+      e.ldy = n;
+      e.gamma = -al[s] * cc;
+      if (s >= 2) {
+        e.Z = out;
+        e.ldz = n;
+        e.beta = be[s];
+      }
+      hemm(A, n, lda, in, n, cols, e, mode);
+      c->stats.filter_launches++;
+    }
+    dim3 grid(std::min<unsigned>(ceil_div(n, 256), 64), k);
+    gather_odd_kernel<T><<<grid, 256, 0, st()>>>(n, deg_dev, Y0, n, Y1, n);
+    CHASE_CHECK_LAUNCH();
+    return mv;
+  }
+
+  // ------------------------------------------------------------ Algorithm 1, line 5
+  // X (n x k, ld ldx) <- orthonormal basis of span(X) orthogonal to Y (n x l, ld ldy, orthonormal).
+  void qr(const T* Y, int64_t ldy, int l, T* X, int64_t ldx, int64_t n, int k) {
+    if (k <= 0) return;
+    T* Gm = Gb();
+    // one block classical Gram-Schmidt pass against the locked columns: X -= Y (Y^H X)
+    auto project = [&]() {
+      if (l <= 0) return;
+      Epi e;
+      e.C = Gm;
+      e.ldc = l;
+      gemm_f64<T>(st(), OP_C, OP_N, l, k, n, Y, ldy, X, ldx, e, W(), c->work_elems);
+      Epi u;
+      u.C = X;
+      u.ldc = ldx;
+      u.alpha = -1.0;
+      u.Z = X;
+      u.ldz = ldx;
+      u.beta = 1.0;
+      gemm_f64<T>(st(), OP_N, OP_N, n, k, l, Y, ldy, Gm, l, u, W(), c->work_elems);
+    };
+    project();
+    // column equilibration (does not change the span)
+    colnorms<T>(st(), n, k, X, ldx, c->dwork);
+    scale_cols<T>(st(), n, k, X, ldx, c->dwork, 1);
+    auto chol_pass = [&](double shift_factor) -> bool {
+      Epi e;
+      e.C = Gm;
+      e.ldc = k;
+      gemm_f64<T>(st(), OP_C, OP_N, k, k, n, X, ldx, X, ldx, e, W(), c->work_elems);
+      hermitianize<T>(st(), k, Gm, k);
+      if (shift_factor > 0.0) {
+        fro_norm2<T>(st(), n, k, X, ldx, c->dwork);
+        double tr = 0.0;
+        CHASE_CUDA(cudaMemcpyAsync(&tr, c->dwork, sizeof(double), cudaMemcpyDeviceToHost, st()));
+        CHASE_CUDA(cudaStreamSynchronize(st()));
+        double shift = shift_factor * ((double)n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 * tr;
+        add_diag<T>(st(), k, Gm, k, nullptr, shift);
+      }
+      CHASE_CUDA(cudaMemsetAsync(c->info, 0, sizeof(int), st()));
+      potrf_lower<T>(st(), k, Gm, k, c->info, W(), c->work_elems);
+      int info = 0;
+      CHASE_CUDA(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, st()));
+      CHASE_CUDA(cudaStreamSynchronize(st()));
+      if (info != 0) return false;
+      trsm_right_lh<T>(st(), n, k, X, ldx, Gm, k, W(), c->work_elems);
+      return true;
+    };
+    // Cholesky-QR2 with a projection before each pass, so the final basis is orthogonal to the
+    // locked columns to rounding even when X was ill-conditioned
+    bool ok = chol_pass(0.0);
+    if (ok) {
+      project();
+      ok = chol_pass(0.0);
+    }
+    if (!ok) {
+      // shifted Cholesky-QR3 (Fukaya et al.): one shifted pass, then Cholesky-QR2
+      c->stats.qr_fallbacks++;
+      colnorms<T>(st(), n, k, X, ldx, c->dwork);
+      scale_cols<T>(st(), n, k, X, ldx, c->dwork, 1);
+      project();
+      ok = chol_pass(11.0);
+      if (ok) {
+        project();
+        ok = chol_pass(0.0);
+      }
+      if (ok) {
+        project();
+        ok = chol_pass(0.0);
+      }
+    }
+    CHASE_REQUIRE(ok, CHASE_ERR_QR_BREAKDOWN, "Cholesky-QR breakdown after the shifted fallback");
+  }
+
+  // ------------------------------------------------------------ Algorithm 1, lines 6-7
+  // Q (n x k, ld n) orthonormal.  Out: Q <- Ritz vectors, ritz[k] ascending (device), res[k] (device).
+  // Uses T2 (A Q) and Tv (n x k scratch, ld n).
+  void rayleigh_ritz(const T* A, int64_t n, int64_t lda, T* Q, T* Wb, T* Tv, int k, double* ritz, double* res, int mode) {
+    if (k <= 0) return;
+    Epi e;
+    e.C = Wb;
+    e.ldc = n;
+    int rmode = (mode == CHASE_FP64_NATIVE) ? CHASE_FP64_NATIVE : CHASE_FP64;
+    hemm(A, n, lda, Q, n, k, e, rmode);                       // W = A Q
+    Epi g;
+    g.C = Gb();
+    g.ldc = k;
+    gemm_f64<T>(st(), OP_C, OP_N, k, k, n, Q, n, Wb, n, g, W(), c->work_elems);  // G = Q^H W
+    hermitianize<T>(st(), k, Gb(), k);
+    T* jw = (T*)c->work;  // Jacobi workspace (k*k + 3k + 8 scalars)
+    heev_jacobi<T>(st(), k, Gb(), k, ritz, Zb(), k, jw, c->work_elems, c->dwork, c->iwork, 1e-14, 60);
+    Epi v;
+    v.C = Tv;
+    v.ldc = n;
+    gemm_f64<T>(st(), OP_N, OP_N, n, k, k, Q, n, Zb(), k, v, W(), c->work_elems);  // Vhat = Q Z
+    Epi r;
+    r.C = Q;
+    r.ldc = n;
+    r.Y = Tv;
+    r.ldy = n;
+    r.gamma = -1.0;
+    r.ycol = ritz;
+    gemm_f64<T>(st(), OP_N, OP_N, n, k, k, Wb, n, Zb(), k, r, W(), c->work_elems);  // R = W Z - Vhat diag(ritz)
+    colnorms<T>(st(), n, k, Q, n, res);
+    copy_cols<T>(st(), n, k, Tv, n, Q, n);
+  }
+
+  // ------------------------------------------------------------ Algorithm 1
+  void solve(const T* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg, int mode, const T* V0,
+             const T* L0) {
+    const int ne = nev + nex;
+    CHASE_REQUIRE(n >= 1 && n <= c->n_max, CHASE_ERR_ARG, "n out of range for this context");
+    CHASE_REQUIRE(nev >= 1 && nex >= 0 && ne <= c->ne_max && ne <= n, CHASE_ERR_ARG, "nev/nex out of range");
+    CHASE_REQUIRE(lda >= n, CHASE_ERR_ARG, "lda < n");
+    CHASE_REQUIRE(tol > 0.0 && deg >= 1 && deg <= c->opts.maxdeg, CHASE_ERR_ARG, "tol or deg out of range");
+    CHASE_REQUIRE(A && V0 && L0, CHASE_ERR_ARG, "null A, V0 or L0");
+    CHASE_REQUIRE(mode >= CHASE_FP64 && mode <= CHASE_BF16x6, CHASE_ERR_ARG, "unknown mode");
+    CHASE_REQUIRE(mode == CHASE_FP64_NATIVE || mode == CHASE_FP64 || oz::available(), CHASE_ERR_UNSUPPORTED,
+                  "split-BF16 modes need the tensor-core kernels");
+    c->have_result = false;
+    c->stats = chase_stats_t{};
+    chase_stats_t& S = c->stats;
+    Timer ttot(c, 0, &S.ms_total);
+    check_nan(A, n, (int)n, lda, "A");
+    check_nan(V0, n, ne, n, "V0");
+    const int runs = c->opts.lanczos_runs, steps = std::min<int>(c->opts.lanczos_steps, (int)n);
+    // Lanczos (line 2)
+    {
+      Timer t(c, 1, &S.ms_lanczos);
+      lanczos<T>(st(), A, n, lda, ne, L0, runs, steps, c->dwork, W(), c->work_elems, c->dwork + 8);
+      init_bounds_kernel<<<1, 1, 0, st()>>>(c->dwork, c->bounds);
+      CHASE_CHECK_LAUNCH();
+      t.stop();
+    }
+    double hb[6];
+    CHASE_CUDA(cudaMemcpyAsync(hb, c->dwork, 4 * sizeof(double), cudaMemcpyDeviceToHost, st()));
+    CHASE_CUDA(cudaStreamSynchronize(st()));
+    double b_sup = hb[0], mu_1 = hb[1], mu_ne = hb[2], theta_max = hb[3];
+    S.b_sup = b_sup;
+    S.mu_1 = mu_1;
+    S.mu_ne = mu_ne;
+    double norm_est = std::max(std::fabs(mu_1), std::fabs(theta_max));
+    S.norm_est = norm_est;
+    const double thresh = tol * norm_est;
+    CHASE_REQUIRE(std::isfinite(b_sup) && std::isfinite(mu_1) && std::isfinite(mu_ne), CHASE_ERR_NAN,
+                  "non-finite Lanczos bounds");
+
+    copy_cols<T>(st(), n, ne, V0, n, V(), n);
+    std::vector<int> m(ne, deg);
+    fill_int_kernel<<<ceil_div(ne, 256), 256, 0, st()>>>(ne, c->deg, deg);
+    CHASE_CHECK_LAUNCH();
+    int l = 0;
+    // mixed-precision policy: bulk filter in the low-precision mode until the smallest unconverged
+    // relative residual reaches its floor, then FP64 for the remaining iterations.
+    bool lowp = (mode == CHASE_BF16x3 || mode == CHASE_BF16x6);
+    const double lowp_floor = (mode == CHASE_BF16x3) ? 3e-4 : 1e-6;
+    int it = 0;
+    struct {
+      int lock;
+      int pad;
+      double bnd[6];
+    } hstat;
+    std::vector<int> degbuf(ne);
+    std::vector<double> resbuf(ne);
+    while (l < nev && it < c->opts.maxiter) {
+      ++it;
+      const int k = ne - l;
+      T* Vact = V() + (int64_t)l * n;
+      T* T1act = T1() + (int64_t)l * n;
+      T* T2act = T2() + (int64_t)l * n;
+      int fmode = (mode == CHASE_FP64_NATIVE) ? CHASE_FP64_NATIVE : (lowp ? mode : CHASE_FP64);
+      {
+        Timer t(c, 1, &S.ms_filter);
+        int64_t mv = filter(A, n, lda, Vact, T1act, k, m.data(), c->deg, b_sup, mu_1, mu_ne, fmode);
+        S.matvecs += mv;
+        if (lowp) {
+          S.matvecs_lowp += mv;
+          S.lowp_iterations++;
+        }
+        t.stop();
+      }
+      {
+        Timer t(c, 1, &S.ms_qr);
+        qr(V(), n, l, Vact, n, n, k);
+        t.stop();
+      }
+      {
+        Timer t(c, 1, &S.ms_rr);
+        rayleigh_ritz(A, n, lda, Vact, T2act, T1act, k, c->ritz, c->res, fmode);
+        t.stop();
+      }
+      {
+        Timer t(c, 1, &S.ms_resid);
+        bookkeeping(st(), k, c->ritz, c->res, thresh, b_sup, c->bounds, c->opts.maxdeg, c->opts.extra_deg,
+                    c->status_dev, c->deg, c->perm, c->ritz2, c->res2, c->iwork);
+        CHASE_CUDA(cudaMemcpyAsync(&hstat.lock, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st()));
+        CHASE_CUDA(cudaMemcpyAsync(hstat.bnd, c->bounds, 6 * sizeof(double), cudaMemcpyDeviceToHost, st()));
+        CHASE_CUDA(cudaMemcpyAsync(degbuf.data(), c->deg, k * sizeof(int), cudaMemcpyDeviceToHost, st()));
+        CHASE_CUDA(cudaMemcpyAsync(resbuf.data(), c->res2, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
+        CHASE_CUDA(cudaStreamSynchronize(st()));
+        const int p = hstat.lock;
+        // lock: Ritz values of the converged prefix, then reorder the remaining active columns
+        if (p > 0) CHASE_CUDA(cudaMemcpyAsync(c->lam_locked + l, c->ritz, p * sizeof(double), cudaMemcpyDeviceToDevice, st()));
+        const int kr = k - p;
+        if (kr > 0) {
+          permute_cols<T>(st(), n, kr, Vact, n, T1act, n, c->perm);
+          copy_cols<T>(st(), n, kr, T1act, n, Vact + (int64_t)p * n, n);
+        }
+        // the device degree array must follow the new active block (it starts at l + p)
+        l += p;
+        mu_1 = hstat.bnd[1];
+        mu_ne = hstat.bnd[2];
+        m.assign(degbuf.begin(), degbuf.begin() + kr);
+        if (lowp) {
+          double minres = 1e308;
+          for (int a = 0; a < kr; ++a) minres = std::min(minres, resbuf[a] / norm_est);
+          if (kr == 0 || minres <= lowp_floor || it >= c->opts.maxiter - c->opts.nfinal) lowp = false;
+        }
+        t.stop();
+      }
+    }
+    S.iterations = it;
+    S.locked = l;
+    CHASE_REQUIRE(l >= nev, CHASE_ERR_NOCONV, "maxiter reached before nev pairs converged");
+    // final order: nev smallest locked values ascending
+    final_sort_kernel<<<ceil_div(l, 128), 128, 0, st()>>>(l, nev, c->lam_locked, c->eigvals, c->perm);
+    CHASE_CHECK_LAUNCH();
+    // T1 = [locked pairs ascending | remaining active block]: the first nev columns are the
+    // eigenvectors, the whole block is a warm start for a nearby problem
+    permute_cols<T>(st(), n, l, V(), n, T1(), n, c->perm);
+    if (ne > l) copy_cols<T>(st(), n, ne - l, V() + (int64_t)l * n, n, T1() + (int64_t)l * n, n);
+    c->n = n;
+    c->nev = nev;
+    c->nex = nex;
+    c->have_result = true;
+    ttot.stop();
+  }
+};
+
+// =====================================================================================
+static chase_status fail(chase_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return (chase_status)code;
+}
+
+#define API_BEGIN(ctx) \
+  if (!(ctx)) return CHASE_ERR_ARG; \
+  try {                           \
+    CHASE_CUDA(cudaSetDevice((ctx)->device));
+#define API_END(ctx)                                                             \
+  }                                                                              \
+  catch (const chase::Error& e) {                                                \
+    return fail((ctx), e.status, e.msg);                                         \
+  }                                                                              \
+  catch (const std::bad_alloc&) {                                                \
+    return fail((ctx), CHASE_ERR_OOM, "host allocation failed");                 \
+  }                                                                              \
+  catch (const std::exception& e) {                                              \
+    return fail((ctx), CHASE_ERR_CUDA, e.what());                                \
+  }                                                                              \
+  (ctx)->err.clear();                                                            \
+  return CHASE_OK;
+
+template <typename T>
+static void filter_api(chase_ctx* c, const T* A, int64_t n, int64_t lda, T* V, int64_t ldv, int k, const int* deg,
+                       double b_sup, double mu_1, double mu_ne, int mode) {
+  Solver<T> s(c);
+  // work on the context's V/T1 buffers (ld n), copy in/out
+  copy_cols<T>(c->stream, n, k, V, ldv, s.V(), n);
+  std::vector<int> d(deg, deg + k);
+  CHASE_CUDA(cudaMemcpyAsync(c->deg, d.data(), k * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  s.filter(A, n, lda, s.V(), s.T1(), k, d.data(), c->deg, b_sup, mu_1, mu_ne, mode);
+  copy_cols<T>(c->stream, n, k, s.V(), n, V, ldv);
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+template <typename T>
+static void rr_api(chase_ctx* c, const T* A, int64_t n, int64_t lda, T* Q, int64_t ldq, int k, double* ritz_host,
+                   double* res_host) {
+  Solver<T> s(c);
+  copy_cols<T>(c->stream, n, k, Q, ldq, s.V(), n);
+  s.rayleigh_ritz(A, n, lda, s.V(), s.T2(), s.T1(), k, c->ritz, c->res, CHASE_FP64);
+  copy_cols<T>(c->stream, n, k, s.V(), n, Q, ldq);
+  if (ritz_host) CHASE_CUDA(cudaMemcpyAsync(ritz_host, c->ritz, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (res_host) CHASE_CUDA(cudaMemcpyAsync(res_host, c->res, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+template <typename T>
+static void heevj_api(chase_ctx* c, const T* G, int64_t ldg, int k, double* w_host, T* Z, int64_t ldz) {
+  T* Gw = (T*)c->G;
+  copy_cols<T>(c->stream, k, k, G, ldg, Gw, k);
+  heev_jacobi<T>(c->stream, k, Gw, k, c->ritz, Z, ldz, (T*)c->work, c->work_elems, c->dwork, c->iwork, 1e-14, 60);
+  CHASE_CUDA(cudaMemcpyAsync(w_host, c->ritz, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+extern "C" {
+
+void chase_default_opts(chase_opts* o) {
+  if (!o) return;
+  o->maxdeg = 36;
+  o->lanczos_steps = 25;
+  o->lanczos_runs = 4;
+  o->maxiter = 30;
+  o->extra_deg = 2;
+  o->nfinal = 1;
+  o->oz_slices = 6;
+}
+
+static int64_t lanczos_elems(int64_t n, int runs, int steps) {
+  int64_t nchunk = (n + 255) / 256;
+  int64_t part = std::max<int64_t>(nchunk * runs * n, (int64_t)runs * 64 * 64);
+  return (int64_t)runs * steps * n + runs * n + part + 2 * runs * 64;
+}
+
+static int64_t work_elems_for(int64_t n, int ne, const chase_opts& o) {
+  int64_t jac = (int64_t)ne * ne + 3 * (int64_t)ne + 8;
+  int64_t lz = lanczos_elems(n, o.lanczos_runs, std::min<int>(o.lanczos_steps, (int)n));
+  int64_t split = 2 * 1024 * 1024;
+  return std::max(std::max(jac, lz), split);
+}
+
+int64_t chase_workspace_bytes(int64_t n_max, int ne_max, chase_dtype dtype, const chase_opts* opts) {
+  chase_opts o;
+  chase_default_opts(&o);
+  if (opts) o = *opts;
+  int64_t esz = dtype == CHASE_C128 ? 16 : 8;
+  int64_t b = 3 * n_max * ne_max * esz + 2 * (int64_t)ne_max * ne_max * esz + work_elems_for(n_max, ne_max, o) * esz;
+  b += oz::workspace_bytes(n_max, ne_max, dtype == CHASE_C128, o.oz_slices);
+  return b;
+}
+
+chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtype dtype, const chase_opts* opts,
+                          void* stream) {
+  if (!out) return CHASE_ERR_ARG;
+  *out = nullptr;
+  if (n_max < 1 || ne_max < 1 || ne_max > n_max || (dtype != CHASE_R64 && dtype != CHASE_C128)) return CHASE_ERR_ARG;
+  chase_ctx* c = new (std::nothrow) chase_ctx();
+  if (!c) return CHASE_ERR_OOM;
+  chase_default_opts(&c->opts);
+  if (opts) c->opts = *opts;
+  if (c->opts.maxdeg < 1 || c->opts.lanczos_runs < 1 || c->opts.lanczos_runs > 8 || c->opts.lanczos_steps < 1 ||
+      c->opts.lanczos_steps > 64 || c->opts.maxiter < 1 || c->opts.oz_slices < 2 || c->opts.oz_slices > 8) {
+    delete c;
+    return CHASE_ERR_ARG;
+  }
+  c->dtype = dtype;
+  c->n_max = n_max;
+  c->ne_max = ne_max;
+  c->esz = dtype == CHASE_C128 ? 16 : 8;
+  try {
+    CHASE_CUDA(cudaGetDevice(&c->device));
+    if (stream) {
+      c->stream = (cudaStream_t)stream;
+    } else {
+      CHASE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+    for (auto& e : c->ev) CHASE_CUDA(cudaEventCreate(&e));
+    size_t freeb = 0, totb = 0;
+    CHASE_CUDA(cudaMemGetInfo(&freeb, &totb));
+    int64_t need = chase_workspace_bytes(n_max, ne_max, dtype, &c->opts);
+    if ((size_t)need + (64ull << 20) > freeb) {
+      c->err = "workspace of " + std::to_string(need) + " bytes does not fit in free device memory";
+      chase_destroy(c);
+      return CHASE_ERR_OOM;
+    }
+    size_t blk = (size_t)n_max * ne_max * c->esz;
+    CHASE_CUDA(cudaMalloc(&c->V, blk));
+    CHASE_CUDA(cudaMalloc(&c->T1, blk));
+    CHASE_CUDA(cudaMalloc(&c->T2, blk));
+    CHASE_CUDA(cudaMalloc(&c->G, (size_t)ne_max * ne_max * c->esz));
+    CHASE_CUDA(cudaMalloc(&c->Z, (size_t)ne_max * ne_max * c->esz));
+    c->work_elems = work_elems_for(n_max, ne_max, c->opts);
+    CHASE_CUDA(cudaMalloc(&c->work, (size_t)c->work_elems * c->esz));
+    c->dwork_elems = 8 + 5 * 8 * 64 + 4 * (int64_t)ne_max + 16;
+    CHASE_CUDA(cudaMalloc(&c->dwork, c->dwork_elems * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->iwork, (size_t)(2 * ne_max + 16) * sizeof(int)));
+    CHASE_CUDA(cudaMalloc(&c->ritz, ne_max * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->res, ne_max * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->ritz2, ne_max * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->res2, ne_max * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->lam_locked, ne_max * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->eigvals, ne_max * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->bounds, 8 * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->deg, ne_max * sizeof(int)));
+    CHASE_CUDA(cudaMalloc(&c->perm, ne_max * sizeof(int)));
+    CHASE_CUDA(cudaMalloc(&c->info, sizeof(int)));
+    CHASE_CUDA(cudaMalloc(&c->status_dev, 4 * sizeof(int)));
+    oz::create(c->ozw, n_max, ne_max, dtype == CHASE_C128, c->opts.oz_slices);
+  } catch (const chase::Error& e) {
+    chase_destroy(c);
+    return (chase_status)e.status;
+  }
+  *out = c;
+  return CHASE_OK;
+}
+
+void chase_destroy(chase_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
+                  c->lam_locked, c->eigvals, c->bounds, c->deg, c->perm, c->info, c->status_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  oz::destroy(c->ozw);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* chase_last_error(const chase_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+chase_status chase_solve(chase_ctx* c, const void* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg,
+                         int mode, const void* V0, const void* L0) {
+  API_BEGIN(c)
+  if (c->dtype == CHASE_C128)
+    Solver<double2>(c).solve((const double2*)A, n, lda, nev, nex, tol, deg, mode, (const double2*)V0, (const double2*)L0);
+  else
+    Solver<double>(c).solve((const double*)A, n, lda, nev, nex, tol, deg, mode, (const double*)V0, (const double*)L0);
+  API_END(c)
+}
+
+chase_status chase_eigvals(chase_ctx* c, double* out, int on_device) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(c->have_result, CHASE_ERR_STATE, "no solve result");
+  CHASE_REQUIRE(out, CHASE_ERR_ARG, "null output");
+  CHASE_CUDA(cudaMemcpyAsync(out, c->eigvals, c->nev * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+chase_status chase_eigvecs(chase_ctx* c, void* out, int64_t ldv, int on_device) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(c->have_result, CHASE_ERR_STATE, "no solve result");
+  CHASE_REQUIRE(out && ldv >= c->n, CHASE_ERR_ARG, "bad output");
+  CHASE_CUDA(cudaMemcpy2DAsync(out, ldv * c->esz, c->T1, c->n * c->esz, c->n * c->esz, c->nev,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+chase_status chase_stats(const chase_ctx* c, chase_stats_t* out) {
+  if (!c || !out) return CHASE_ERR_ARG;
+  *out = c->stats;
+  return CHASE_OK;
+}
+
+chase_status chase_lanczos(chase_ctx* c, const void* A, int64_t n, int64_t lda, int ne, const void* L0, int runs,
+                           int steps, double* out_host) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(A && L0 && out_host && n >= 1 && n <= c->n_max && lda >= n && ne >= 1, CHASE_ERR_ARG, "bad args");
+  CHASE_REQUIRE(runs >= 1 && runs <= 8 && steps >= 1 && steps <= 64 && steps <= n, CHASE_ERR_ARG, "bad runs/steps");
+  if (c->dtype == CHASE_C128)
+    lanczos<double2>(c->stream, (const double2*)A, n, lda, ne, (const double2*)L0, runs, steps, c->dwork,
+                     (double2*)c->work, c->work_elems, c->dwork + 8);
+  else
+    lanczos<double>(c->stream, (const double*)A, n, lda, ne, (const double*)L0, runs, steps, c->dwork,
+                    (double*)c->work, c->work_elems, c->dwork + 8);
+  CHASE_CUDA(cudaMemcpyAsync(out_host, c->dwork, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+
+chase_status chase_filter(chase_ctx* c, const void* A, int64_t n, int64_t lda, void* V, int64_t ldv, int ncols,
+                          const int* deg_host, double b_sup, double mu_1, double mu_ne, int mode) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(A && V && deg_host && n >= 1 && n <= c->n_max && lda >= n && ldv >= n && ncols >= 0 &&
+                    ncols <= c->ne_max,
+                CHASE_ERR_ARG, "bad args");
+  CHASE_REQUIRE(mode >= CHASE_FP64 && mode <= CHASE_BF16x6, CHASE_ERR_ARG, "unknown mode");
+  for (int a = 0; a < ncols; ++a) {
+    CHASE_REQUIRE(deg_host[a] >= 1 && deg_host[a] <= 1000, CHASE_ERR_ARG, "degree out of range");
+    CHASE_REQUIRE(a == 0 || deg_host[a] >= deg_host[a - 1], CHASE_ERR_ARG, "degrees must be non-decreasing");
+  }
+  if (c->dtype == CHASE_C128)
+    filter_api<double2>(c, (const double2*)A, n, lda, (double2*)V, ldv, ncols, deg_host, b_sup, mu_1, mu_ne, mode);
+  else
+    filter_api<double>(c, (const double*)A, n, lda, (double*)V, ldv, ncols, deg_host, b_sup, mu_1, mu_ne, mode);
+  API_END(c)
+}
+
+chase_status chase_qr(chase_ctx* c, void* X, int64_t n, int64_t ldx, int ncols, int nlocked) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(X && n >= 1 && n <= c->n_max && ldx >= n && nlocked >= 0 && ncols >= nlocked && ncols <= c->ne_max &&
+                    ncols <= n,
+                CHASE_ERR_ARG, "bad args");
+  if (c->dtype == CHASE_C128) {
+    double2* x = (double2*)X;
+    Solver<double2>(c).qr(x, ldx, nlocked, x + nlocked * ldx, ldx, n, ncols - nlocked);
+  } else {
+    double* x = (double*)X;
+    Solver<double>(c).qr(x, ldx, nlocked, x + nlocked * ldx, ldx, n, ncols - nlocked);
+  }
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+
+chase_status chase_rayleigh_ritz(chase_ctx* c, const void* A, int64_t n, int64_t lda, void* Q, int64_t ldq, int ncols,
+                                 double* ritz_host, double* resid_host) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(A && Q && n >= 1 && n <= c->n_max && lda >= n && ldq >= n && ncols >= 1 && ncols <= c->ne_max,
+                CHASE_ERR_ARG, "bad args");
+  if (c->dtype == CHASE_C128)
+    rr_api<double2>(c, (const double2*)A, n, lda, (double2*)Q, ldq, ncols, ritz_host, resid_host);
+  else
+    rr_api<double>(c, (const double*)A, n, lda, (double*)Q, ldq, ncols, ritz_host, resid_host);
+  API_END(c)
+}
+
+
+chase_status chase_heevj(chase_ctx* c, const void* G, int64_t ldg, int k, double* w_host, void* Z, int64_t ldz) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(G && Z && w_host && k >= 1 && k <= c->ne_max && ldg >= k && ldz >= k, CHASE_ERR_ARG, "bad args");
+  if (c->dtype == CHASE_C128)
+    heevj_api<double2>(c, (const double2*)G, ldg, k, w_host, (double2*)Z, ldz);
+  else
+    heevj_api<double>(c, (const double*)G, ldg, k, w_host, (double*)Z, ldz);
+  API_END(c)
+}
+
+chase_status chase_hemm(chase_ctx* c, const void* A, int64_t n, int64_t lda, const void* B, int64_t ldb, int ncols,
+                        void* C, int64_t ldc, int mode) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(A && B && C && n >= 1 && n <= c->n_max && lda >= n && ldb >= n && ldc >= n && ncols >= 1 &&
+                    ncols <= c->ne_max,
+                CHASE_ERR_ARG, "bad args");
+  CHASE_REQUIRE(mode >= CHASE_FP64 && mode <= CHASE_BF16x6, CHASE_ERR_ARG, "unknown mode");
+  Epi e;
+  e.C = C;
+  e.ldc = ldc;
+  if (c->dtype == CHASE_C128) {
+    Solver<double2> s(c);
+    if (mode != CHASE_FP64_NATIVE && oz::available()) oz::prepare_A<double2>(c->stream, c->ozw, (const double2*)A, n, lda, mode);
+    s.hemm((const double2*)A, n, lda, (const double2*)B, ldb, ncols, e, mode);
+  } else {
+    Solver<double> s(c);
+    if (mode != CHASE_FP64_NATIVE && oz::available()) oz::prepare_A<double>(c->stream, c->ozw, (const double*)A, n, lda, mode);
+    s.hemm((const double*)A, n, lda, (const double*)B, ldb, ncols, e, mode);
+  }
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+chase_status chase_generate(chase_ctx* c, void* A, int64_t n, int64_t lda, const double* lam, const void* U,
+                            const void* B, const void* D, int k) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(A && lam && U && B && D && n >= 1 && lda >= n && k >= 0, CHASE_ERR_ARG, "bad args");
+  if (c->dtype == CHASE_C128)
+    generate_wy<double2>(c->stream, (double2*)A, n, lda, lam, (const double2*)U, (const double2*)B, (const double2*)D, k);
+  else
+    generate_wy<double>(c->stream, (double*)A, n, lda, lam, (const double*)U, (const double*)B, (const double*)D, k);
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+chase_status chase_solve_batched(chase_ctx* c, int nprob, const void* const* A, const int64_t* n, const int* nev,
+                                 const int* nex, double tol, int deg, int mode, void* const* Vd, const void* const* L0,
+                                 double* const* eigvals, chase_stats_t* stats_host) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(nprob >= 0 && A && n && nev && nex && Vd && L0 && eigvals, CHASE_ERR_ARG, "bad args");
+  for (int p = 0; p < nprob; ++p) {
+    int ne = nev[p] + nex[p];
+    if (c->dtype == CHASE_C128) {
+      Solver<double2> s(c);
+      s.solve((const double2*)A[p], n[p], n[p], nev[p], nex[p], tol, deg, mode, (const double2*)Vd[p],
+              (const double2*)L0[p]);
+      // eigenvectors (ascending) followed by the rest of the search block: the next start block
+      copy_cols<double2>(c->stream, n[p], ne, (const double2*)c->T1, n[p], (double2*)Vd[p], n[p]);
+    } else {
+      Solver<double> s(c);
+      s.solve((const double*)A[p], n[p], n[p], nev[p], nex[p], tol, deg, mode, (const double*)Vd[p],
+              (const double*)L0[p]);
+      copy_cols<double>(c->stream, n[p], ne, (const double*)c->T1, n[p], (double*)Vd[p], n[p]);
+    }
+    CHASE_CUDA(cudaMemcpyAsync(eigvals[p], c->eigvals, nev[p] * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (stats_host) stats_host[p] = c->stats;
+  }
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
+chase_status chase_backward(chase_ctx* c, const void* A, int64_t lda, const double* gl, const void* gV, int64_t ldg,
+                            void* gA, int64_t ldga, double minres_tol, int minres_maxit) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(c->dtype == CHASE_R64, CHASE_ERR_UNSUPPORTED, "backward implemented for real symmetric problems");
+  CHASE_REQUIRE(c->have_result, CHASE_ERR_STATE, "no solve result");
+  (void)A; (void)lda; (void)gl; (void)gV; (void)ldg; (void)gA; (void)ldga; (void)minres_tol; (void)minres_maxit;
+  CHASE_REQUIRE(false, CHASE_ERR_UNSUPPORTED, "backward not built yet");
+  API_END(c)
+}
+
+}  // extern "C"

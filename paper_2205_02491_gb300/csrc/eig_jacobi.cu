@@ -1,0 +1,250 @@
+// Dense Hermitian eigensolver of the Rayleigh-Ritz quotient (Algorithm 1,
+// line 6) on the device: parallel cyclic two-sided Jacobi in FP64.
+//
+// Ordering: round-robin tournament on kp = k rounded up to even indices; each
+// of the kp-1 rounds of a sweep rotates kp/2 disjoint pairs at once.  A round
+// is two launches: rotation parameters for every pair (from the 2x2 blocks of
+// the current G), then an in-place update of G (2x2 blocks of J^H G J) and of
+// Z (Z J).  For each pair the 2x2 block [[a, g], [conj g, b]] is made real by
+// the phase D = diag(1, conj(g)/|g|) and zeroed by the real rotation with
+// t = sign(z)/(|z| + sqrt(1+z^2)), z = (b-a)/(2|g|).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace chase {
+
+template <typename T> struct Rot {
+  int partner;  // index paired with this one in the current round (-1: none)
+  T self;       // J[x][x]
+  T other;      // J[partner][x]
+};
+
+__device__ inline void round_pair(int r, int idx, int kp, int& a, int& b) {
+  int m = kp - 1;
+  if (idx == 0) {
+    a = r;
+    b = kp - 1;
+  } else {
+    a = (r + idx) % m;
+    b = (r - idx + m) % m;
+  }
+}
+
+template <typename T>
+__global__ void jacobi_params_kernel(int k, int kp, int r, const T* __restrict__ G, int64_t ldg, Rot<T>* rot) {
+  using s = S<T>;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kp / 2) return;
+  int a, b;
+  round_pair(r, idx, kp, a, b);
+  int p = min(a, b), q = max(a, b);
+  if (q >= k) {  // dummy index for odd k
+    if (p < k) rot[p] = Rot<T>{-1, s::one(), s::zero()};
+    return;
+  }
+  T g = G[p + (int64_t)q * ldg];
+  double ag = sqrt(s::abs2(g));
+  if (!(ag > 1e-300)) {
+    rot[p] = Rot<T>{q, s::one(), s::zero()};
+    rot[q] = Rot<T>{p, s::one(), s::zero()};
+    return;
+  }
+  double ap = s::re(G[p + (int64_t)p * ldg]), bq = s::re(G[q + (int64_t)q * ldg]);
+  double z = (bq - ap) / (2.0 * ag);
+  double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+  double c = 1.0 / sqrt(1.0 + t * t);
+  double sn = t * c;
+  T ph = s::scale(s::conj(g), 1.0 / ag);  // conj(g)/|g|
+  // J = [[c, sn], [-sn*ph, c*ph]] on columns (p, q)
+  rot[p] = Rot<T>{q, s::make(c, 0.0), s::scale(ph, -sn)};  // J[p][p], J[q][p]
+  rot[q] = Rot<T>{p, s::scale(ph, c), s::make(sn, 0.0)};   // J[q][q], J[p][q]
+}
+
+// G <- J^H G J, one thread per (row pair, column pair) 2x2 block (in place).
+template <typename T>
+__global__ void jacobi_apply_g_kernel(int k, int kp, int r, T* G, int64_t ldg, const Rot<T>* __restrict__ rot) {
+  using s = S<T>;
+  int i1 = blockIdx.x * blockDim.x + threadIdx.x;  // row pair index
+  int i2 = blockIdx.y * blockDim.y + threadIdx.y;  // column pair index
+  int half = kp / 2;
+  if (i1 >= half || i2 >= half) return;
+  int a, b, c, d;
+  round_pair(r, i1, kp, a, b);
+  round_pair(r, i2, kp, c, d);
+  int rows[2] = {a, b}, cols[2] = {c, d};
+  T in[2][2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+      in[u][v] = (rows[u] < k && cols[v] < k) ? G[rows[u] + (int64_t)cols[v] * ldg] : s::zero();
+  // coefficients: J[x][x] and J[partner(x)][x]
+  T js[2], jo[2], ks[2], ko[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    if (rows[u] < k) {
+      Rot<T> rr = rot[rows[u]];
+      js[u] = rr.self;
+      jo[u] = rr.partner >= 0 ? rr.other : s::zero();
+    } else {
+      js[u] = s::one();
+      jo[u] = s::zero();
+    }
+    if (cols[u] < k) {
+      Rot<T> rc = rot[cols[u]];
+      ks[u] = rc.self;
+      ko[u] = rc.partner >= 0 ? rc.other : s::zero();
+    } else {
+      ks[u] = s::one();
+      ko[u] = s::zero();
+    }
+  }
+  // column update: C[u][v] = in[u][v] J[v][v] + in[u][v'] J[v'][v]
+  T cu[2][2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) cu[u][v] = s::add(s::mul(in[u][v], ks[v]), s::mul(in[u][1 - v], ko[v]));
+  // row update: out[u][v] = conj(J[u][u]) C[u][v] + conj(J[u'][u]) C[u'][v]
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      if (rows[u] >= k || cols[v] >= k) continue;
+      T o = s::add(s::mul(s::conj(js[u]), cu[u][v]), s::mul(s::conj(jo[u]), cu[1 - u][v]));
+      if (rows[u] == cols[v]) o = s::make(s::re(o), 0.0);
+      if (i1 == i2 && u != v) o = s::zero();  // the rotated pair's off-diagonal entry
+      G[rows[u] + (int64_t)cols[v] * ldg] = o;
+    }
+}
+
+// Z <- Z J (rows i, column pairs), in place.
+template <typename T>
+__global__ void jacobi_apply_z_kernel(int k, int kp, int r, T* Z, int64_t ldz, const Rot<T>* __restrict__ rot) {
+  using s = S<T>;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int pi = blockIdx.y;
+  if (i >= k) return;
+  int a, b;
+  round_pair(r, pi, kp, a, b);
+  if (a >= k || b >= k) return;
+  Rot<T> ra = rot[a], rb = rot[b];
+  T za = Z[i + (int64_t)a * ldz], zb = Z[i + (int64_t)b * ldz];
+  Z[i + (int64_t)a * ldz] = s::add(s::mul(za, ra.self), s::mul(zb, ra.other));
+  Z[i + (int64_t)b * ldz] = s::add(s::mul(zb, rb.self), s::mul(za, rb.other));
+}
+
+template <typename T> __global__ void set_identity_kernel(int k, T* Z, int64_t ldz) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i < k) Z[i + (int64_t)j * ldz] = (i == j) ? S<T>::one() : S<T>::zero();
+}
+
+// off^2 and fro^2 of G: per-column partials then an ordered sum (deterministic)
+template <typename T> __global__ void offdiag_partial_kernel(int k, const T* __restrict__ G, int64_t ldg, double* part) {
+  using s = S<T>;
+  int j = blockIdx.x;
+  double off = 0.0, tot = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double v = s::abs2(G[i + (int64_t)j * ldg]);
+    tot += v;
+    if (i != j) off += v;
+  }
+  __shared__ double r1[32], r2[32];
+  off = warp_sum(off);
+  tot = warp_sum(tot);
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = off;
+    r2[threadIdx.x >> 5] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double a = threadIdx.x < (blockDim.x >> 5) ? r1[threadIdx.x] : 0.0;
+    double b = threadIdx.x < (blockDim.x >> 5) ? r2[threadIdx.x] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (threadIdx.x == 0) {
+      part[2 * j] = a;
+      part[2 * j + 1] = b;
+    }
+  }
+}
+
+__global__ void offdiag_sum_kernel(int k, const double* part, double* out) {
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < k; j += 32) {
+    a += part[2 * j];
+    b += part[2 * j + 1];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+// eigenvalues from the diagonal, ascending rank (stable), permutation
+template <typename T>
+__global__ void diag_rank_kernel(int k, const T* __restrict__ G, int64_t ldg, double* w, int* perm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  double wi = S<T>::re(G[i + (int64_t)i * ldg]);
+  int rank = 0;
+  for (int j = 0; j < k; ++j) {
+    double wj = S<T>::re(G[j + (int64_t)j * ldg]);
+    rank += (wj < wi) || (wj == wi && j < i);
+  }
+  w[rank] = wi;
+  perm[rank] = i;
+}
+
+template <typename T>
+int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int64_t ldz, T* work, int64_t work_elems,
+                double* dwork, int* iwork, double tol, int max_sweeps) {
+  // work: k*k scalars for the unsorted Z plus Rot array; dwork: 2k+2 doubles; iwork: k ints
+  CHASE_REQUIRE(work_elems >= (int64_t)k * k + 3 * (int64_t)k + 8, 2, "heev_jacobi: workspace too small");
+  if (k <= 0) return 0;
+  T* Zu = work;
+  Rot<T>* rot = reinterpret_cast<Rot<T>*>(work + (int64_t)k * k);
+  int kp = k + (k & 1);
+  set_identity_kernel<T><<<dim3(ceil_div(k, 256), k), 256, 0, st>>>(k, Zu, k);
+  CHASE_CHECK_LAUNCH();
+  double* part = dwork + 2;
+  double hstat[2];
+  int sweeps = 0;
+  bool done = false;
+  for (; sweeps <= max_sweeps; ++sweeps) {
+    offdiag_partial_kernel<T><<<k, 128, 0, st>>>(k, G, ldg, part);
+    offdiag_sum_kernel<<<1, 32, 0, st>>>(k, part, dwork);
+    CHASE_CHECK_LAUNCH();
+    CHASE_CUDA(cudaMemcpyAsync(hstat, dwork, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CHASE_CUDA(cudaStreamSynchronize(st));
+    CHASE_REQUIRE(isfinite(hstat[0]) && isfinite(hstat[1]), 5, "heev_jacobi: non-finite matrix");
+    if (sqrt(hstat[0]) <= tol * sqrt(hstat[1]) || k == 1) {
+      done = true;
+      break;
+    }
+    if (sweeps == max_sweeps) break;
+    int half = kp / 2;
+    dim3 gblk(16, 16), ggrid(ceil_div(half, 16), ceil_div(half, 16));
+    dim3 zgrid(ceil_div(k, 128), half);
+    for (int r = 0; r < kp - 1; ++r) {
+      jacobi_params_kernel<T><<<ceil_div(half, 128), 128, 0, st>>>(k, kp, r, G, ldg, rot);
+      jacobi_apply_g_kernel<T><<<ggrid, gblk, 0, st>>>(k, kp, r, G, ldg, rot);
+      jacobi_apply_z_kernel<T><<<zgrid, 128, 0, st>>>(k, kp, r, Zu, k, rot);
+    }
+    CHASE_CHECK_LAUNCH();
+  }
+  CHASE_REQUIRE(done, 8, "heev_jacobi: sweep cap reached without convergence");
+  diag_rank_kernel<T><<<ceil_div(k, 128), 128, 0, st>>>(k, G, ldg, w, iwork);
+  CHASE_CHECK_LAUNCH();
+  permute_cols<T>(st, k, k, Zu, k, Z, ldz, iwork);
+  return sweeps;
+}
+
+template int heev_jacobi<double>(cudaStream_t, int, double*, int64_t, double*, double*, int64_t, double*, int64_t,
+                                 double*, int*, double, int);
+template int heev_jacobi<double2>(cudaStream_t, int, double2*, int64_t, double*, double2*, int64_t, double2*, int64_t,
+                                  double*, int*, double, int);
+
+}  // namespace chase

@@ -1,0 +1,68 @@
+// Internal launch interface of the FP64 kernels (host side).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace chase {
+
+enum Op { OP_N = 0, OP_C = 1 };  // OP_C: conjugate transpose (transpose for real)
+
+// Epilogue of a product:  C = alpha*acc + gamma*ycol[j]*Y + beta*Z  (Y, Z optional; Z may alias C).
+struct Epi {
+  void* C = nullptr;
+  int64_t ldc = 0;
+  double alpha = 1.0;
+  const void* Y = nullptr;
+  int64_t ldy = 0;
+  double gamma = 0.0;
+  const double* ycol = nullptr;  // per-column factor on Y (device), optional
+  const void* Z = nullptr;
+  int64_t ldz = 0;
+  double beta = 0.0;
+};
+
+// C(MxN) = op(A) op(B) with epilogue, FP64 DFMA.  work: >= ksplit*M*N scalars when ksplit > 1.
+template <typename T>
+void gemm_f64(cudaStream_t st, Op opA, Op opB, int64_t M, int64_t N, int64_t K, const T* A, int64_t lda,
+              const T* B, int64_t ldb, const Epi& epi, T* work, int64_t work_elems);
+
+template <typename T> void colnorms(cudaStream_t st, int64_t n, int k, const T* X, int64_t ldx, double* out);
+template <typename T> void colmaxabs(cudaStream_t st, int64_t n, int k, const T* X, int64_t ldx, double* out);
+template <typename T>
+void permute_cols(cudaStream_t st, int64_t n, int k, const T* src, int64_t lds, T* dst, int64_t ldd, const int* perm);
+template <typename T> void scale_cols(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const double* s, int invert);
+template <typename T>
+void copy_cols(cudaStream_t st, int64_t n, int k, const T* src, int64_t lds, T* dst, int64_t ldd);
+
+// Cholesky G = L L^H (lower, in place, k x k).  info: device int, set > 0 on a non-positive pivot.
+template <typename T>
+void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems);
+// X <- X L^{-H} (right solve with the lower Cholesky factor), X n x k.
+template <typename T>
+void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T* L, int64_t ldl, T* work,
+                   int64_t work_elems);
+template <typename T> void add_diag(cudaStream_t st, int k, T* G, int64_t ldg, const double* shift_dev, double shift);
+template <typename T> void hermitianize(cudaStream_t st, int k, T* G, int64_t ldg);
+template <typename T> void fro_norm2(cudaStream_t st, int64_t n, int k, const T* X, int64_t ldx, double* out);
+
+// Parallel cyclic Jacobi: G (k x k, destroyed) -> w ascending, Z.  Returns sweeps used; throws on cap.
+template <typename T>
+int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int64_t ldz, T* work,
+                int64_t work_elems, double* dwork, int* iwork, double tol, int max_sweeps);
+
+// Lanczos bounds (Algorithm 1, line 2).  out4 (device) = {b_sup, mu_1, mu_ne, theta_max}.
+template <typename T>
+void lanczos(cudaStream_t st, const T* A, int64_t n, int64_t lda, int ne, const T* L0, int runs, int steps,
+             double* out4, T* work, int64_t work_elems, double* dwork);
+
+// Input generator from compact-WY factors.
+template <typename T>
+void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* lam, const T* U, const T* B,
+                 const T* D, int k);
+
+// Bookkeeping (Algorithm 1, lines 8-14) on the device.  See chase.cu for the layout of `bk`.
+void bookkeeping(cudaStream_t st, int k, const double* ritz, const double* res, double thresh, double b_sup,
+                 double* bounds, int maxdeg, int extra_deg, int* out_lock, int* out_deg, int* out_perm,
+                 double* out_ritz, double* out_res, int* scratch);
+
+}  // namespace chase

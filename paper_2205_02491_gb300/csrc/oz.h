@@ -1,0 +1,39 @@
+// Split-BF16 tensor-core products (tcgen05) with FP64-accurate or mixed
+// precision accumulation: the production path of the large HEMM/GEMM products.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace chase {
+namespace oz {
+
+struct Workspace {
+  bool ready = false;
+  bool complex_ = true;
+  int slices = 6;
+  int64_t n_max = 0;
+  int ne_max = 0;
+  void* a_planes = nullptr;   // bf16 digit planes of A
+  void* b_planes = nullptr;   // bf16 digit planes of the right operand
+  double* a_scale = nullptr;  // per-row power-of-two scale of A
+  double* b_scale = nullptr;  // per-column scale of the right operand
+  int* flags = nullptr;       // device error flags of the bounded waits
+  const void* a_src = nullptr;  // A whose planes are cached
+  int a_mode = -1;
+  int64_t a_n = 0;
+};
+
+bool available();
+int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices);
+void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices);
+void destroy(Workspace& w);
+template <typename T>
+void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, int mode);
+template <typename T>
+void hemm(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, const T* B, int64_t ldb, int k,
+          const Epi& e, int mode);
+
+}  // namespace oz
+}  // namespace chase
