@@ -66,7 +66,7 @@ typedef struct {
   int maxiter;         /* outer iterations before CHASE_ERR_NOCONV (default 30) */
   int extra_deg;       /* constant added to the optimised degree (default 2) */
   int nfinal;          /* mixed modes: minimum FP64 sweeps at the end (default 1) */
-  int oz_slices;       /* FP64 mode: BF16 slices per operand (default 6) */
+  int oz_slices;       /* FP64 mode: BF16 slices per operand, 6 or 7 (default 7) */
 } chase_opts;
 
 typedef struct {

@@ -10,6 +10,8 @@
 // iteration too, Section "Offloading Selected Routines to GPUs").
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -81,6 +83,15 @@ struct Timer {
     *acc += ms;
   }
 };
+
+bool verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("CHASE_VERBOSE");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
 
 void filter_coeffs(double b_sup, double mu_1, double mu_ne, int mmax, double& c, double& e, std::vector<double>& al,
                    std::vector<double>& be) {
@@ -179,6 +190,7 @@ template <typename T> struct Solver {
     if (mode == CHASE_FP64_NATIVE || !oz::available()) {
       gemm_f64<T>(st(), OP_N, OP_N, n, k, n, A, lda, B, ldb, e, W(), c->work_elems);
     } else {
+      oz::prepare_A<T>(st(), c->ozw, A, n, lda, mode);  // cached per A within a call
       oz::hemm<T>(st(), c->ozw, A, n, lda, B, ldb, k, e, mode);
     }
   }
@@ -193,7 +205,6 @@ template <typename T> struct Solver {
     double cc, ee;
     std::vector<double> al, be;
     filter_coeffs(b_sup, mu_1, mu_ne, mmax, cc, ee, al, be);
-    if (mode != CHASE_FP64_NATIVE && oz::available()) oz::prepare_A<T>(st(), c->ozw, A, n, lda, mode);
     T* B[2] = {Y0, Y1};
     int f = 0;
     int64_t mv = 0;
@@ -346,6 +357,7 @@ template <typename T> struct Solver {
                   "split-BF16 modes need the tensor-core kernels");
     c->have_result = false;
     c->stats = chase_stats_t{};
+    oz::invalidate(c->ozw);  // A may hold new values at the same address
     chase_stats_t& S = c->stats;
     Timer ttot(c, 0, &S.ms_total);
     check_nan(A, n, (int)n, lda, "A");
@@ -379,8 +391,12 @@ template <typename T> struct Solver {
     int l = 0;
     // mixed-precision policy: bulk filter in the low-precision mode until the smallest unconverged
     // relative residual reaches its floor, then FP64 for the remaining iterations.
+    // mixed modes: bulk filter in split-BF16 while it still makes progress; switch to FP64 for
+    // the rest once the smallest unconverged relative residual reaches the bulk precision floor
+    // or stops falling by at least a factor 4 per iteration
     bool lowp = (mode == CHASE_BF16x3 || mode == CHASE_BF16x6);
-    const double lowp_floor = (mode == CHASE_BF16x3) ? 3e-4 : 1e-6;
+    const double lowp_floor = (mode == CHASE_BF16x3) ? 1e-3 : 3e-5;
+    double prev_minres = 1e308;
     int it = 0;
     struct {
       int lock;
@@ -425,6 +441,7 @@ template <typename T> struct Solver {
         CHASE_CUDA(cudaMemcpyAsync(degbuf.data(), c->deg, k * sizeof(int), cudaMemcpyDeviceToHost, st()));
         CHASE_CUDA(cudaMemcpyAsync(resbuf.data(), c->res2, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
         CHASE_CUDA(cudaStreamSynchronize(st()));
+        CHASE_REQUIRE(oz::read_flags(st(), c->ozw) == 0, CHASE_ERR_TIMEOUT, "a tensor-core product hit its wait limit");
         const int p = hstat.lock;
         // lock: Ritz values of the converged prefix, then reorder the remaining active columns
         if (p > 0) CHASE_CUDA(cudaMemcpyAsync(c->lam_locked + l, c->ritz, p * sizeof(double), cudaMemcpyDeviceToDevice, st()));
@@ -438,10 +455,23 @@ template <typename T> struct Solver {
         mu_1 = hstat.bnd[1];
         mu_ne = hstat.bnd[2];
         m.assign(degbuf.begin(), degbuf.begin() + kr);
+        if (verbose()) {
+          double mr = 0.0, mn = 1e308;
+          for (int a = 0; a < kr; ++a) {
+            mr = std::max(mr, resbuf[a] / norm_est);
+            mn = std::min(mn, resbuf[a] / norm_est);
+          }
+          fprintf(stderr, "[chase] it=%d mode=%d k=%d locked=%d(+%d) mu1=%.6g mune=%.6g res[min,max]=%.3e,%.3e deg[0,last]=%d,%d fallbacks=%d ms[filter,qr,rr,resid]=%.1f,%.1f,%.1f,%.1f\n",
+                  it, fmode, k, l, p, mu_1, mu_ne, mn, mr, kr ? m[0] : 0, kr ? m[kr - 1] : 0, S.qr_fallbacks,
+                  S.ms_filter, S.ms_qr, S.ms_rr, S.ms_resid);
+        }
         if (lowp) {
           double minres = 1e308;
           for (int a = 0; a < kr; ++a) minres = std::min(minres, resbuf[a] / norm_est);
-          if (kr == 0 || minres <= lowp_floor || it >= c->opts.maxiter - c->opts.nfinal) lowp = false;
+          if (kr == 0 || minres <= lowp_floor || minres > 0.25 * prev_minres ||
+              it >= c->opts.maxiter - c->opts.nfinal)
+            lowp = false;
+          prev_minres = minres;
         }
         t.stop();
       }
@@ -492,6 +522,7 @@ template <typename T>
 static void filter_api(chase_ctx* c, const T* A, int64_t n, int64_t lda, T* V, int64_t ldv, int k, const int* deg,
                        double b_sup, double mu_1, double mu_ne, int mode) {
   Solver<T> s(c);
+  oz::invalidate(c->ozw);
   // work on the context's V/T1 buffers (ld n), copy in/out
   copy_cols<T>(c->stream, n, k, V, ldv, s.V(), n);
   std::vector<int> d(deg, deg + k);
@@ -505,6 +536,7 @@ template <typename T>
 static void rr_api(chase_ctx* c, const T* A, int64_t n, int64_t lda, T* Q, int64_t ldq, int k, double* ritz_host,
                    double* res_host) {
   Solver<T> s(c);
+  oz::invalidate(c->ozw);
   copy_cols<T>(c->stream, n, k, Q, ldq, s.V(), n);
   s.rayleigh_ritz(A, n, lda, s.V(), s.T2(), s.T1(), k, c->ritz, c->res, CHASE_FP64);
   copy_cols<T>(c->stream, n, k, s.V(), n, Q, ldq);
@@ -532,7 +564,7 @@ void chase_default_opts(chase_opts* o) {
   o->maxiter = 30;
   o->extra_deg = 2;
   o->nfinal = 1;
-  o->oz_slices = 6;
+  o->oz_slices = 7;
 }
 
 static int64_t lanczos_elems(int64_t n, int runs, int steps) {
@@ -762,16 +794,13 @@ chase_status chase_hemm(chase_ctx* c, const void* A, int64_t n, int64_t lda, con
   Epi e;
   e.C = C;
   e.ldc = ldc;
-  if (c->dtype == CHASE_C128) {
-    Solver<double2> s(c);
-    if (mode != CHASE_FP64_NATIVE && oz::available()) oz::prepare_A<double2>(c->stream, c->ozw, (const double2*)A, n, lda, mode);
-    s.hemm((const double2*)A, n, lda, (const double2*)B, ldb, ncols, e, mode);
-  } else {
-    Solver<double> s(c);
-    if (mode != CHASE_FP64_NATIVE && oz::available()) oz::prepare_A<double>(c->stream, c->ozw, (const double*)A, n, lda, mode);
-    s.hemm((const double*)A, n, lda, (const double*)B, ldb, ncols, e, mode);
-  }
+  oz::invalidate(c->ozw);
+  if (c->dtype == CHASE_C128)
+    Solver<double2>(c).hemm((const double2*)A, n, lda, (const double2*)B, ldb, ncols, e, mode);
+  else
+    Solver<double>(c).hemm((const double*)A, n, lda, (const double*)B, ldb, ncols, e, mode);
   CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  CHASE_REQUIRE(oz::read_flags(c->stream, c->ozw) == 0, CHASE_ERR_TIMEOUT, "a tensor-core product hit its wait limit");
   API_END(c)
 }
 

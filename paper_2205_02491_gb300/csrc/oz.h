@@ -29,6 +29,8 @@ bool available();
 int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices);
 void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices);
 void destroy(Workspace& w);
+void invalidate(Workspace& w);
+int read_flags(cudaStream_t st, Workspace& w);
 template <typename T>
 void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, int mode);
 template <typename T>

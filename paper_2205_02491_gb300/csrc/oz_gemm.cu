@@ -1,0 +1,749 @@
+// Split-BF16 tensor-core products on sm_103a (tcgen05 + TMEM + TMA).
+//
+// Every FP64 operand is scaled by a power of two per row (left operand) or per
+// column (right operand) to |x| <= 1 and split into S signed 8-bit digits,
+// x = sum_t d_t 2^(-7-8t), d_t integer in [-128, 128].  Plane t stores
+// d_t 2^(-8t) in bf16 (exact).  A product of plane t and plane u lands on level
+// L = t + u with unit 2^(-8L); all products of one level share that grid, so a
+// level's FP32 partial sum over a chunk of 96 K values is an exact integer
+// (|sum| < 2^24: at most 10 products of magnitude <= 2^14 per K value).
+//
+//   FP64 mode (S = 7 by default, levels 0..6; S = 6 optional): levels 0..4
+//   accumulate in their own TMEM accumulators (MMA N = 80) and are flushed
+//   exactly every 96 K into one int64 register per output (units 2^-32, no
+//   overflow for K <= 65472); the remaining levels share one FP32 accumulator over
+//   the whole K.  Each tensor-core accumulation step truncates to about 24 bits
+//   of the running sum (measured), so the error of a shared accumulator grows
+//   with the number of steps times its magnitude; keeping five levels exact
+//   leaves only terms below 2^-40 there.  Truncation after level S-1 is below 2^-(8S-8) relative
+//   to |row max| * |col max| per product (S = 7: 2^-56, errors comparable to DFMA).
+//   Mixed modes (S = 2: 3 products, S = 3: 6 products): one FP32 accumulator.
+//
+// Complex operands use real tiles: with B1 = [Yr | Yi] and B2 = [-Yi | Yr]
+// (N = 2 x 64 columns) one accumulator of width 128 holds [Cr | Ci] =
+// Ar B1 + Ai B2.  A is the Hermitian matrix of the eigenproblem, whose K-major
+// rows are the conjugated columns of its column-major storage.
+//
+// Kernel roles (320 threads): warp 0 lane 0 issues TMA loads, warp 1 lane 0
+// issues tcgen05.mma, warps 2..9 (2 groups of 4 warps covering the 4 TMEM lane
+// quadrants, half of the accumulator columns each) run
+// the exact-level flushes and the fused FP64 epilogue
+//   C = alpha * acc + gamma * ycol[j] * Y + beta * Z.
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA sets
+// an error flag, drains its copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "oz.h"
+
+namespace chase {
+namespace oz {
+
+constexpr int BM = 128;          // output rows per tile (TMEM lanes)
+constexpr int BK = 32;           // K per k-block: 64 bytes of bf16 (64B swizzle atom)
+constexpr int B_STAGES = 2;      // right-operand k-blocks (all slices)
+constexpr int KB_PER_CHUNK = 3;  // exact levels flushed every 96 K
+constexpr int NTHREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int EPI_WARP0 = 2;
+constexpr int EPI_WARPS = 8;
+constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
+
+template <int S, int NEX, bool CPLX> struct Cfg {
+  static constexpr int NT = NEX > 0 ? 80 : 128;    // accumulator width (MMA N)
+  static constexpr int AP = CPLX ? 2 : 1;          // left planes per slice (re, im)
+  static constexpr int BP = CPLX ? 3 : 1;          // right planes per slice (-im, re, im)
+  static constexpr int NCOLS = CPLX ? NT / 2 : NT; // output columns per tile
+  static constexpr int BROWS = NCOLS;              // right-operand rows (N index) per plane box
+  static constexpr int A_PLANE = BM * BK * 2;      // 8 KB
+  static constexpr int A_SLOT = AP * A_PLANE;
+  static constexpr int B_PLANE = BROWS * BK * 2;
+  static constexpr int B_SLICE = BP * B_PLANE;
+  static constexpr int B_BYTES = S * B_SLICE;                 // bytes landed per k-block
+  static constexpr int B_STAGE = (B_BYTES + 1023) / 1024 * 1024;  // stage stride (1 KB aligned)
+  static constexpr int SMEM_LIMIT = 232448 - 1024 - 256;
+  static constexpr int A_FIT = (SMEM_LIMIT - B_STAGES * B_STAGE) / A_SLOT;
+  static constexpr int A_SLOTS = A_FIT < 8 ? A_FIT : 8;  // ring of left-operand slices (>= S)
+  static constexpr int NACC = NEX + 1;
+  static constexpr int TMEM_USED = NACC * NT;
+  static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : (TMEM_USED <= 256 ? 256 : 512);
+  static constexpr int EPI_COLS = NT / 2;          // accumulator columns per epilogue thread (2 groups)
+  static constexpr int SMEM_OPS = B_STAGES * B_STAGE + A_SLOTS * A_SLOT;
+  static constexpr int SMEM_BYTES = SMEM_OPS + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int MAXLEVEL = S - 1;
+  static_assert(TMEM_USED <= 512, "TMEM");
+  static_assert(SMEM_BYTES <= 232448, "shared memory");
+  static_assert(A_SLOTS >= S, "a k-block's slices must fit in the ring");
+  static_assert(EPI_COLS % 8 == 0, "epilogue loads 8 columns at a time");
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done;
+}
+
+// bounded wait: false on timeout or when another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_sh, int* err) {
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 255) {
+      if (*abort_sh) return false;
+      unsigned long long t = globaltimer();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > TIMEOUT_NS) {
+        *abort_sh = 1;
+        atomicOr(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          dst),
+      "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// K-major operand tile with 64-byte swizzle: 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)4 << 61;             // 64-byte swizzle
+  return d;
+}
+
+// kind::f16, bf16 x bf16 -> f32, K-major A and B, M = 128, N = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- kernel
+struct EpiArgs {
+  void* C;
+  int64_t ldc;
+  double alpha;
+  const void* Y;
+  int64_t ldy;
+  double gamma;
+  const double* ycol;
+  const void* Z;
+  int64_t ldz;
+  double beta;
+};
+
+// slices of the left operand in processing order: descending, so that the
+// first MMAs of every k-block go to the inexact accumulator while the epilogue
+// flushes the exact ones
+template <int S, int NEX, bool CPLX>
+__global__ void __maxnreg__(168)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                   int K, const double* __restrict__ a_scale, const double* __restrict__ b_scale, EpiArgs ep,
+                   int* err) {
+  using Cf = Cfg<S, NEX, CPLX>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sB = smem;
+  unsigned char* sA = smem + B_STAGES * Cf::B_STAGE;
+  uint64_t* bars = (uint64_t*)(sA + Cf::A_SLOTS * Cf::A_SLOT);
+  // barrier layout
+  uint64_t* a_full = bars;                    // Cf::A_SLOTS
+  uint64_t* a_empty = a_full + Cf::A_SLOTS;       // Cf::A_SLOTS
+  uint64_t* b_full = a_empty + Cf::A_SLOTS;       // B_STAGES
+  uint64_t* b_empty = b_full + B_STAGES;      // B_STAGES
+  uint64_t* chunk_full = b_empty + B_STAGES;  // 1
+  uint64_t* tmem_empty = chunk_full + 1;      // 1
+  uint64_t* drain = tmem_empty + 1;           // 1
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_sh = (volatile int*)(tmem_slot + 1);
+
+  // a CTA of a launch that already hit a wait limit does nothing
+  if (*(volatile int*)err != 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tile = blockIdx.x, m_tile = blockIdx.y;
+  const int m0 = m_tile * BM, n0 = n_tile * Cf::NCOLS;
+  const int nkb = (K + BK - 1) / BK;
+  const int nchunks = (nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < Cf::A_SLOTS; ++i) {
+      mbar_init(smem_u32(&a_full[i]), 1);
+      mbar_init(smem_u32(&a_empty[i]), 1);
+    }
+    for (int i = 0; i < B_STAGES; ++i) {
+      mbar_init(smem_u32(&b_full[i]), 1);
+      mbar_init(smem_u32(&b_empty[i]), 1);
+    }
+    mbar_init(smem_u32(chunk_full), 1);
+    mbar_init(smem_u32(tmem_empty), EPI_WARPS);
+    mbar_init(smem_u32(drain), 1);
+    *abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(Cf::TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ TMA producer
+    int a_iter = 0, b_issued = 0;
+    bool ok = true;
+    for (int kb = 0; kb < nkb && ok; ++kb) {
+      const int k0 = kb * BK;
+      const int bs = kb % B_STAGES;
+      if (!mbar_wait(smem_u32(&b_empty[bs]), ((kb / B_STAGES) & 1) ^ 1, abort_sh, err)) {
+        ok = false;
+        break;
+      }
+      ++b_issued;
+      mbar_expect_tx(smem_u32(&b_full[bs]), Cf::B_BYTES);
+      for (int u = 0; u < S; ++u)
+        for (int p = 0; p < Cf::BP; ++p)
+          tma_load_3d(smem_u32(sB + bs * Cf::B_STAGE + u * Cf::B_SLICE + p * Cf::B_PLANE), &tmB,
+                      smem_u32(&b_full[bs]), k0, n0, u * Cf::BP + p);
+      for (int ti = 0; ti < S; ++ti, ++a_iter) {
+        const int t = S - 1 - ti;
+        const int as = a_iter % Cf::A_SLOTS;
+        if (!mbar_wait(smem_u32(&a_empty[as]), ((a_iter / Cf::A_SLOTS) & 1) ^ 1, abort_sh, err)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(smem_u32(&a_full[as]), Cf::A_SLOT);
+        for (int p = 0; p < Cf::AP; ++p)
+          tma_load_3d(smem_u32(sA + as * Cf::A_SLOT + p * Cf::A_PLANE), &tmA, smem_u32(&a_full[as]), k0, m0,
+                      t * Cf::AP + p);
+      }
+    }
+    // drain: every issued copy must have landed before the CTA exits
+    for (int i = 0; i < B_STAGES; ++i) {
+      int uses = b_issued / B_STAGES + (i < b_issued % B_STAGES ? 1 : 0);
+      if (uses > 0) {
+        unsigned long long t0 = globaltimer();
+        while (!mbar_try(smem_u32(&b_full[i]), (uses - 1) & 1) && globaltimer() - t0 < TIMEOUT_NS) {
+        }
+      }
+    }
+    for (int i = 0; i < Cf::A_SLOTS; ++i) {
+      int uses = a_iter / Cf::A_SLOTS + (i < a_iter % Cf::A_SLOTS ? 1 : 0);
+      if (uses > 0) {
+        unsigned long long t0 = globaltimer();
+        while (!mbar_try(smem_u32(&a_full[i]), (uses - 1) & 1) && globaltimer() - t0 < TIMEOUT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------------ MMA issuer
+    constexpr uint32_t IDESC = idesc_bf16(BM, Cf::NT);
+    bool first[Cf::NACC];
+#pragma unroll
+    for (int a = 0; a < Cf::NACC; ++a) first[a] = true;
+    int a_iter = 0;
+    bool ok = true;
+    // all MMAs of pair (t, u) over this k-block's two K-steps into accumulator acc
+    auto issue_pair = [&](uint32_t abase, uint32_t bbase, int t, int u) {
+      const int level = t + u;
+      const int acc = level < NEX ? level : NEX;
+      const uint32_t dt = tmem + (uint32_t)(acc * Cf::NT);
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        const uint32_t koff = ks * 32;
+        if (CPLX) {
+          const uint32_t b_slice = bbase + u * Cf::B_SLICE;
+          // [Cr | Ci] += Ar [Yr | Yi] + Ai [-Yi | Yr]
+          mma_bf16(dt, sw64_desc(abase + koff), sw64_desc(b_slice + Cf::B_PLANE + koff), IDESC, first[acc] ? 0u : 1u);
+          first[acc] = false;
+          mma_bf16(dt, sw64_desc(abase + Cf::A_PLANE + koff), sw64_desc(b_slice + koff), IDESC, 1u);
+        } else {
+          mma_bf16(dt, sw64_desc(abase + koff), sw64_desc(bbase + u * Cf::B_SLICE + koff), IDESC, first[acc] ? 0u : 1u);
+          first[acc] = false;
+        }
+      }
+    };
+    for (int kb = 0; kb < nkb && ok; ++kb) {
+      const int bs = kb % B_STAGES;
+      const int chunk = kb / KB_PER_CHUNK;
+      const bool chunk_start = (kb % KB_PER_CHUNK) == 0;
+      if (!mbar_wait(smem_u32(&b_full[bs]), (kb / B_STAGES) & 1, abort_sh, err)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      if (chunk_start)
+        for (int a = 0; a < NEX; ++a) first[a] = true;
+      const uint32_t bbase = smem_u32(sB + bs * Cf::B_STAGE);
+      if (!(NEX > 0 && chunk_start && chunk > 0)) {
+        // one pass: slices in descending order, pairs of each slice inexact-first
+        for (int ti = 0; ti < S && ok; ++ti, ++a_iter) {
+          const int t = S - 1 - ti;
+          const int as = a_iter % Cf::A_SLOTS;
+          if (!mbar_wait(smem_u32(&a_full[as]), (a_iter / Cf::A_SLOTS) & 1, abort_sh, err)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t abase = smem_u32(sA + as * Cf::A_SLOT);
+          for (int u = Cf::MAXLEVEL - t; u >= 0; --u) issue_pair(abase, bbase, t, u);
+          mma_commit(smem_u32(&a_empty[as]));
+        }
+      } else {
+        // first k-block of a chunk: every inexact pair of the k-block runs while the epilogue
+        // flushes the exact accumulators of the previous chunk, then the exact pairs
+        for (int ti = 0; ti < S && ok; ++ti) {
+          const int t = S - 1 - ti;
+          const int as = (a_iter + ti) % Cf::A_SLOTS;
+          if (!mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t abase = smem_u32(sA + as * Cf::A_SLOT);
+          for (int u = Cf::MAXLEVEL - t; u >= 0 && t + u >= NEX; --u) issue_pair(abase, bbase, t, u);
+        }
+        if (ok && !mbar_wait(smem_u32(tmem_empty), (chunk - 1) & 1, abort_sh, err)) ok = false;
+        if (!ok) break;
+        fence_after();
+        for (int ti = 0; ti < S; ++ti, ++a_iter) {
+          const int t = S - 1 - ti;
+          const int as = a_iter % Cf::A_SLOTS;
+          const uint32_t abase = smem_u32(sA + as * Cf::A_SLOT);
+          for (int u = (NEX - 1 - t < Cf::MAXLEVEL - t ? NEX - 1 - t : Cf::MAXLEVEL - t); u >= 0; --u)
+            issue_pair(abase, bbase, t, u);
+          mma_commit(smem_u32(&a_empty[as]));
+        }
+      }
+      if (!ok) break;
+      mma_commit(smem_u32(&b_empty[bs]));
+      // exact levels: one commit per chunk (the epilogue consumes each before the next
+      // chunk's exact MMAs start); single-accumulator modes: one commit at the end
+      if ((NEX > 0 && (kb % KB_PER_CHUNK) == KB_PER_CHUNK - 1) || kb == nkb - 1) mma_commit(smem_u32(chunk_full));
+    }
+    // drain all MMAs before TMEM can be freed
+    mma_commit(smem_u32(drain));
+    unsigned long long t0 = globaltimer();
+    while (!mbar_try(smem_u32(drain), 0) && globaltimer() - t0 < TIMEOUT_NS) {
+    }
+  } else if (warp >= EPI_WARP0) {
+    // ------------------------------------------------------------ epilogue
+    constexpr int EPI_COLS = Cf::EPI_COLS;
+    const int ew = warp - EPI_WARP0;
+    const int wg = ew >> 2;        // accumulator columns [EPI_COLS wg, EPI_COLS (wg + 1))
+    const int q = warp & 3;        // TMEM lane quadrant
+    const int row = q * 32 + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+    // exact levels 0..NEX-1 summed as one integer in units of level NEX-1's grid
+    // (2^-32 for NEX = 5).  Per chunk |sum| <= 1.5 2^53, so K <= 65472 cannot overflow.
+    long long acc64[NEX > 0 ? EPI_COLS : 1];
+#pragma unroll
+    for (int j = 0; j < (NEX > 0 ? EPI_COLS : 1); ++j) acc64[j] = 0;
+    bool ok = true;
+    const int nwait = NEX > 0 ? nchunks : 1;
+    for (int ch = 0; ch < nwait; ++ch) {
+      if (!mbar_wait(smem_u32(chunk_full), ch & 1, abort_sh, err)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      if (NEX > 0) {
+#pragma unroll
+        for (int h = 0; h < EPI_COLS / 8; ++h) {
+          long long part[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) part[j] = 0;
+#pragma unroll
+          for (int L = 0; L < (NEX > 0 ? NEX : 1); ++L) {
+            uint32_t r[8];
+            tmem_ld8(lane_addr + (uint32_t)(L * Cf::NT + wg * EPI_COLS + h * 8), r);
+            const float sc = (float)(1ull << (8 * L));  // level L unit is 2^-8L
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const long long iv = (long long)__float2int_rn(__uint_as_float(r[j]) * sc);
+              part[j] += iv << (8 * (NEX - 1 - L));
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc64[h * 8 + j] += part[j];
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(tmem_empty));
+      }
+    }
+    if (ok) {
+      const int gi = m0 + row;
+#pragma unroll
+      for (int h = 0; h < EPI_COLS / 8; ++h) {
+        uint32_t r[8];
+        tmem_ld8(lane_addr + (uint32_t)(NEX * Cf::NT + wg * EPI_COLS + h * 8), r);
+        if (gi >= M) continue;
+        const double rs = a_scale[gi];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = h * 8 + jj;
+          const int c = wg * EPI_COLS + j;
+          int gj, part;
+          if (CPLX) {
+            gj = n0 + (c % Cf::NCOLS);
+            part = c / Cf::NCOLS;
+          } else {
+            gj = n0 + c;
+            part = 0;
+          }
+          if (gj >= N) continue;
+          double v = (double)__uint_as_float(r[jj]);
+          if (NEX > 0) v += (double)acc64[NEX > 0 ? j : 0] * 2.3283064365386963e-10;  // 2^-32
+          v *= rs * b_scale[gj] * 6.103515625e-05;                                   // 2^-14
+          const int comp = CPLX ? 2 : 1;
+          double out = ep.alpha * v;
+          if (ep.Y) {
+            const double g = ep.gamma * (ep.ycol ? ep.ycol[gj] : 1.0);
+            out += g * ((const double*)ep.Y)[(gi + (int64_t)gj * ep.ldy) * comp + part];
+          }
+          if (ep.Z) out += ep.beta * ((const double*)ep.Z)[(gi + (int64_t)gj * ep.ldz) * comp + part];
+          ((double*)ep.C)[(gi + (int64_t)gj * ep.ldc) * comp + part] = out;
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cf::TMEM_COLS));
+}
+
+// ---------------------------------------------------------------- split kernels
+// Per-column power-of-two scale s = 2^e with max|re|,|im| = f 2^e, f in [0.5, 1).
+template <typename T>
+__global__ void col_scale_kernel(int64_t K, const T* __restrict__ X, int64_t ldx, double* scale) {
+  const T* x = X + (int64_t)blockIdx.x * ldx;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < K; i += blockDim.x) {
+    T v = x[i];
+    m = fmax(m, fmax(fabs(S<T>::re(v)), fabs(S<T>::im(v))));
+  }
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+    int e = 0;
+    if (v > 0.0 && isfinite(v)) frexp(v, &e);
+    scale[blockIdx.x] = v > 0.0 ? ldexp(1.0, e) : 1.0;
+  }
+}
+
+// Digits of one value: d_t = rint(r_t), r_0 = x/s * 2^7, r_{t+1} = (r_t - d_t) 2^8; plane stores d_t 2^-8t.
+template <int NS> __device__ __forceinline__ void digits(double xs, __nv_bfloat16 (&out)[NS]) {
+  double r = xs * 128.0;
+  float sc = 1.0f;
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    double d = rint(r);
+    out[t] = __float2bfloat16_rn((float)d * sc);
+    r = (r - d) * 256.0;
+    sc *= 0.00390625f;
+  }
+}
+
+// Left-operand planes (K-major rows = conjugated columns of X when conj, else columns):
+// plane (t, p), p in {re, im}.  Right-operand planes: p in {-im, re, im}.
+// Real: one plane per slice.  Layout planes[(t*P + p) * ncols + col][Kpad].
+template <typename T, int NS, int KIND>
+__global__ void split_cols_kernel(int64_t K, int64_t Kpad, int ncols, const T* __restrict__ X, int64_t ldx,
+                                  const double* __restrict__ scale, int conj, __nv_bfloat16* planes) {
+  constexpr bool CPLX = S<T>::cplx;
+  const int col = blockIdx.y;
+  const T* x = X + (int64_t)col * ldx;
+  const double inv = 1.0 / scale[col];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < K; i += (int64_t)gridDim.x * blockDim.x) {
+    T v = x[i];
+    double re = S<T>::re(v) * inv;
+    double im = (conj ? -S<T>::im(v) : S<T>::im(v)) * inv;
+    __nv_bfloat16 dr[NS], di[NS];
+    digits<NS>(re, dr);
+    if (CPLX) digits<NS>(im, di);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      if (!CPLX) {
+        planes[((int64_t)t * ncols + col) * Kpad + i] = dr[t];
+      } else if (KIND == 0) {
+        planes[((int64_t)(t * 2 + 0) * ncols + col) * Kpad + i] = dr[t];
+        planes[((int64_t)(t * 2 + 1) * ncols + col) * Kpad + i] = di[t];
+      } else {
+        planes[((int64_t)(t * 3 + 0) * ncols + col) * Kpad + i] = __hneg(di[t]);
+        planes[((int64_t)(t * 3 + 1) * ncols + col) * Kpad + i] = dr[t];
+        planes[((int64_t)(t * 3 + 2) * ncols + col) * Kpad + i] = di[t];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                             const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                             CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+  });
+  return fn;
+}
+
+static CUtensorMap make_map(const void* base, int64_t K, int64_t Kpad, int64_t rows, int planes, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kpad * 2), (cuuint64_t)(Kpad * 2 * rows)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  EncodeFn fn = encode_fn();
+  CHASE_REQUIRE(fn != nullptr, 9, "cuTensorMapEncodeTiled unavailable");
+  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CHASE_REQUIRE(r == CUDA_SUCCESS, 6, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+static int slices_for(int mode, int fp64_slices) {
+  if (mode == 2) return 2;   // BF16x3
+  if (mode == 3) return 3;   // BF16x6
+  return fp64_slices;        // FP64
+}
+
+static int64_t kpad(int64_t K) { return (K + 7) / 8 * 8; }
+
+bool available() {
+  static int ok = -1;
+  if (ok < 0) {
+    int dev = 0, major = 0, minor = 0;
+    ok = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+      ok = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+  }
+  return ok == 1;
+}
+
+int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices) {
+  int ap = complex_ ? 2 : 1, bp = complex_ ? 3 : 1;
+  int64_t kp = kpad(n_max);
+  int64_t a = (int64_t)slices * ap * n_max * kp * 2;
+  int64_t b = (int64_t)slices * bp * ne_max * kp * 2;
+  return a + b + (n_max + ne_max) * 8 + 64;
+}
+
+void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices) {
+  w.n_max = n_max;
+  w.ne_max = ne_max;
+  w.complex_ = complex_;
+  w.slices = slices;
+  if (!available()) return;
+  int ap = complex_ ? 2 : 1, bp = complex_ ? 3 : 1;
+  int64_t kp = kpad(n_max);
+  CHASE_CUDA(cudaMalloc(&w.a_planes, (size_t)slices * ap * n_max * kp * 2));
+  CHASE_CUDA(cudaMalloc(&w.b_planes, (size_t)slices * bp * ne_max * kp * 2));
+  CHASE_CUDA(cudaMalloc(&w.a_scale, n_max * sizeof(double)));
+  CHASE_CUDA(cudaMalloc(&w.b_scale, ne_max * sizeof(double)));
+  CHASE_CUDA(cudaMalloc(&w.flags, 16 * sizeof(int)));
+  CHASE_CUDA(cudaMemset(w.flags, 0, 16 * sizeof(int)));
+  w.ready = true;
+}
+
+void destroy(Workspace& w) {
+  void* ps[] = {w.a_planes, w.b_planes, w.a_scale, w.b_scale, w.flags};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  w = Workspace{};
+}
+
+template <typename T>
+void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, int mode) {
+  CHASE_REQUIRE(w.ready, 9, "split products not initialised");
+  // planes of all slices are nested: the S-slice split's first slices are the 2- and 3-slice splits
+  if (w.a_src == (const void*)A && w.a_n == n && w.a_mode == w.slices) return;
+  (void)mode;
+  const int S_ = w.slices;
+  int64_t kp = kpad(n);
+  col_scale_kernel<T><<<(unsigned)n, 256, 0, st>>>(n, A, lda, w.a_scale);
+  CHASE_CHECK_LAUNCH();
+  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 32), (unsigned)n);
+  // A Hermitian: K-major row i of A = conjugate of column i of its column-major storage
+#define SPLIT(SS) split_cols_kernel<T, SS, 0><<<grid, 256, 0, st>>>(n, kp, (int)n, A, lda, w.a_scale, 1, (__nv_bfloat16*)w.a_planes)
+  switch (S_) {
+    case 6: SPLIT(6); break;
+    case 7: SPLIT(7); break;
+    default: CHASE_REQUIRE(false, 1, "oz_slices must be 6 or 7");
+  }
+#undef SPLIT
+  CHASE_CHECK_LAUNCH();
+  w.a_src = A;
+  w.a_n = n;
+  w.a_mode = w.slices;
+}
+
+void invalidate(Workspace& w) {
+  w.a_src = nullptr;
+  w.a_n = 0;
+  w.a_mode = -1;
+  if (w.flags) CHASE_CUDA(cudaMemset(w.flags, 0, 16 * sizeof(int)));  // a new call starts clean
+}
+
+template <int S, int NEX, bool CPLX>
+static void launch(cudaStream_t st, Workspace& w, int64_t n, int k, int a_slices, const Epi& e) {
+  using Cf = Cfg<S, NEX, CPLX>;
+  int64_t kp = kpad(n);
+  const int ap = CPLX ? 2 : 1, bp = CPLX ? 3 : 1;
+  // A planes were split with w.slices slices: only the first S are read (nested digits)
+  CUtensorMap ma = make_map(w.a_planes, n, kp, n, a_slices * ap, BM);
+  CUtensorMap mb = make_map(w.b_planes, n, kp, k, S * bp, Cf::BROWS);
+  static bool attr_set = false;
+  if (!attr_set) {
+    CHASE_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Cf::SMEM_BYTES));
+    attr_set = true;
+  }
+  EpiArgs ea{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
+  dim3 grid(ceil_div(k, Cf::NCOLS), ceil_div(n, BM));
+  oz_gemm_kernel<S, NEX, CPLX><<<grid, NTHREADS, Cf::SMEM_BYTES, st>>>(ma, mb, (int)n, k, (int)n, w.a_scale,
+                                                                         w.b_scale, ea, w.flags);
+  CHASE_CHECK_LAUNCH();
+}
+
+template <typename T>
+void hemm(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, const T* B, int64_t ldb, int k,
+          const Epi& e, int mode) {
+  CHASE_REQUIRE(w.ready, 9, "split products not initialised");
+  CHASE_REQUIRE(w.a_src == (const void*)A && w.a_n == n, 7, "prepare_A must precede hemm");
+  CHASE_REQUIRE(k <= w.ne_max && n <= w.n_max, 1, "hemm size exceeds the workspace");
+  CHASE_REQUIRE(n <= 65472, 1, "split products support K <= 65472 (int64 exact-level sums)");
+  constexpr bool CPLX = S<T>::cplx;
+  const int S_ = slices_for(mode, w.slices);
+  int64_t kp = kpad(n);
+  col_scale_kernel<T><<<(unsigned)k, 256, 0, st>>>(n, B, ldb, w.b_scale);
+  CHASE_CHECK_LAUNCH();
+  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 32), (unsigned)k);
+#define SPLITB(SS) split_cols_kernel<T, SS, 1><<<grid, 256, 0, st>>>(n, kp, k, B, ldb, w.b_scale, 0, (__nv_bfloat16*)w.b_planes)
+  switch (S_) {
+    case 2: SPLITB(2); break;
+    case 3: SPLITB(3); break;
+    case 6: SPLITB(6); break;
+    case 7: SPLITB(7); break;
+    default: CHASE_REQUIRE(false, 1, "unsupported slice count");
+  }
+#undef SPLITB
+  CHASE_CHECK_LAUNCH();
+  if (S_ == 7) launch<7, 5, CPLX>(st, w, n, k, w.slices, e);
+  else if (S_ == 6) launch<6, 5, CPLX>(st, w, n, k, w.slices, e);
+  else if (S_ == 3) launch<3, 0, CPLX>(st, w, n, k, w.slices, e);
+  else launch<2, 0, CPLX>(st, w, n, k, w.slices, e);
+}
+
+int read_flags(cudaStream_t st, Workspace& w) {
+  if (!w.ready) return 0;
+  int f = 0;
+  CHASE_CUDA(cudaMemcpyAsync(&f, w.flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CHASE_CUDA(cudaStreamSynchronize(st));
+  return f;
+}
+
+template void prepare_A<double>(cudaStream_t, Workspace&, const double*, int64_t, int64_t, int);
+template void prepare_A<double2>(cudaStream_t, Workspace&, const double2*, int64_t, int64_t, int);
+template void hemm<double>(cudaStream_t, Workspace&, const double*, int64_t, int64_t, const double*, int64_t, int,
+                           const Epi&, int);
+template void hemm<double2>(cudaStream_t, Workspace&, const double2*, int64_t, int64_t, const double2*, int64_t, int,
+                            const Epi&, int);
+
+}  // namespace oz
+}  // namespace chase

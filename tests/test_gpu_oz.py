@@ -1,0 +1,136 @@
+"""Split-BF16 tensor-core products (tcgen05) against exact products and the oracle."""
+import numpy as np
+import pytest
+
+from gen import problems as G
+from oracle import chase_oracle as O
+from tests.helpers import dev, host, subspace_sin
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2205_02491_gb300 as P
+    return P
+
+
+def _rel_err(C, ref, A, B):
+    # error relative to the per-row / per-column scales the split uses, per K term
+    ra = np.max(np.maximum(np.abs(A.real), np.abs(A.imag)), axis=1)
+    cb = np.max(np.maximum(np.abs(B.real), np.abs(B.imag)), axis=0)
+    return np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / A.shape[1]
+
+
+def _exact(A, B):
+    # A B in extended precision (complex via longdouble real parts)
+    Ar = np.real(A).astype(np.longdouble)
+    Ai = np.imag(A).astype(np.longdouble)
+    Br = np.real(B).astype(np.longdouble)
+    Bi = np.imag(B).astype(np.longdouble)
+    return (Ar @ Br - Ai @ Bi).astype(np.float64) + 1j * (Ar @ Bi + Ai @ Br).astype(np.float64)
+
+
+@pytest.mark.parametrize("n,k", [(300, 70), (129, 1), (1000, 130)])
+def test_hemm_fp64_split_complex(pkg, n, k):
+    p = G.problem_small(n, 2, 2, complex_=True, seed_pid=n + 1)
+    A = p.dense()
+    B = G.gaussian(np.random.default_rng(n), (n, k), True)
+    s = pkg.Chase(n, k, complex_=True)
+    C = host(s.hemm(dev(A), dev(B), "fp64"))
+    ref = _exact(A, B)
+    assert _rel_err(C, ref, A, B) <= 2.0 ** -49
+
+
+@pytest.mark.parametrize("n,k", [(257, 200), (64, 3)])
+def test_hemm_fp64_split_real(pkg, n, k):
+    p = G.problem_small(n, 2, 2, complex_=False, seed_pid=n + 2)
+    A = p.dense()
+    B = np.random.default_rng(n).standard_normal((n, k))
+    s = pkg.Chase(n, k, complex_=False)
+    C = host(s.hemm(dev(A), dev(B), "fp64"))
+    ref = (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
+    ra = np.max(np.abs(A), axis=1)
+    cb = np.max(np.abs(B), axis=0)
+    assert np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / n <= 2.0 ** -49
+
+
+def test_exact_levels_at_worst_case_sums(pkg):
+    # all-positive operands near the row/column maxima make every level sum as large as the
+    # exactness bound allows; an inexact FP32 level sum would show up as ~2^-24 relative error
+    n, k = 1024, 64
+    g = np.random.default_rng(3)
+    X = g.uniform(0.995, 1.0, (n, n)) + 1j * g.uniform(0.995, 1.0, (n, n))
+    A = 0.5 * (X + np.conj(X.T))
+    B = g.uniform(0.995, 1.0, (n, k)) - 1j * g.uniform(0.995, 1.0, (n, k))
+    s = pkg.Chase(n, k, complex_=True)
+    C = host(s.hemm(dev(A), dev(B), "fp64"))
+    ref = _exact(A, B)
+    assert np.max(np.abs(C - ref) / np.abs(ref)) <= 1e-14
+
+
+@pytest.mark.parametrize("mode,bound", [("bf16x3", 2.0 ** -13), ("bf16x6", 2.0 ** -20)])
+def test_hemm_mixed_modes(pkg, mode, bound):
+    n, k = 512, 96
+    p = G.problem_small(n, 2, 2, complex_=True, seed_pid=5)
+    A = p.dense()
+    B = G.gaussian(np.random.default_rng(9), (n, k), True)
+    s = pkg.Chase(n, k, complex_=True)
+    C = host(s.hemm(dev(A), dev(B), mode))
+    ref = _exact(A, B)
+    assert _rel_err(C, ref, A, B) <= bound
+
+
+def test_filter_fp64_split_vs_oracle(pkg):
+    n, k = 400, 33
+    p = G.problem_small(n, 10, 23, complex_=True, seed_pid=12)
+    A = p.dense()
+    V = p.V0[:, :k]
+    m = np.sort(np.random.default_rng(2).integers(1, 37, size=k))
+    ref, _ = O.chebyshev_filter(A, V, m, 1.05, -1.0, -0.7)
+    s = pkg.Chase(n, k, complex_=True)
+    Vt = dev(V)
+    s.filter(dev(A), Vt, m, 1.05, -1.0, -0.7, "fp64")
+    out = host(Vt)
+    scale = np.max(np.abs(ref), axis=0)
+    assert np.max(np.abs(out - ref) / scale[None, :]) <= 1e-11
+
+
+def _solve(pkg, p, mode, A):
+    s = pkg.Chase(p.n, p.ne, complex_=p.complex_)
+    w, Vt = s.solve(dev(A), p.nev, p.nex, p.tol, p.deg, mode, dev(p.V0), dev(p.L0))
+    return w.cpu().numpy(), host(Vt), s.stats()
+
+
+@pytest.mark.parametrize("cplx,n,nev,nex", [(True, 96, 8, 4), (False, 300, 12, 6), (True, 700, 20, 10)])
+def test_solve_fp64_split_vs_oracle(pkg, cplx, n, nev, nex):
+    p = G.problem_small(n, nev, nex, complex_=cplx, seed_pid=n + 7)
+    A = p.dense()
+    ref = O.chase_solve(A, nev, nex, p.tol, p.deg, p.maxdeg, p.V0, p.L0, p.lanczos_steps)
+    w, V, st = _solve(pkg, p, "fp64", A)
+    nrm = p.norm2()
+    assert np.max(np.abs(w - ref.eigvals)) <= 1e-10 * nrm
+    R = A @ V - V * w[None, :]
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
+    assert abs(st["iterations"] - ref.iterations) <= 1
+
+
+@pytest.mark.parametrize("mode", ["fp64", "bf16x3", "bf16x6"])
+def test_solve_c1_modes(pkg, mode):
+    p = G.problem_c1()
+    A = p.dense()
+    ref = O.chase_solve(A, p.nev, p.nex, p.tol, p.deg, p.maxdeg, p.V0, p.L0, p.lanczos_steps)
+    w, V, st = _solve(pkg, p, mode, A)
+    nrm = p.norm2()
+    assert np.max(np.abs(w - ref.eigvals)) <= 1e-10 * nrm
+    assert np.max(np.abs(w - p.lam[:p.nev])) <= 1e-10 * nrm
+    R = G.implicit_matvec(p.lam, p.U, V) - V * w[None, :]
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
+    E = G.exact_eigvecs(p.U, np.arange(p.nev))
+    gap = p.lam[p.nev] - p.lam[p.nev - 1]
+    assert subspace_sin(E, V) <= max(1e-8, 1.01 * np.linalg.norm(R) / gap)
+    if mode != "fp64":
+        assert st["lowp_iterations"] >= 1
