@@ -67,6 +67,8 @@ typedef struct {
   int extra_deg;       /* constant added to the optimised degree (default 2) */
   int nfinal;          /* mixed modes: minimum FP64 sweeps at the end (default 1) */
   int oz_slices;       /* FP64 mode: BF16 slices per operand, 6 or 7 (default 7) */
+  int native_below_mflop; /* products below this many MFLOP use DFMA kernels; 0: always
+                             split tensor-core products (default 2000) */
 } chase_opts;
 
 typedef struct {

@@ -409,6 +409,46 @@ void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T
   }
 }
 
+// ============================================================== triangular inverse
+// Inverse of one CB x CB lower-triangular diagonal block in place (one block per CTA).
+template <typename T> __global__ void trtri_diag_kernel(int k, T* L, int64_t ldl) {
+  using s = S<T>;
+  __shared__ T a[CB][CB + 1];
+  __shared__ T x[CB][CB + 1];
+  const int j0 = blockIdx.x * CB;
+  const int nb = min(CB, k - j0);
+  const int i = threadIdx.x, j = threadIdx.y;
+  T* Lb = L + j0 + (int64_t)j0 * ldl;
+  if (i < nb && j < nb) a[i][j] = (j <= i) ? Lb[i + (int64_t)j * ldl] : s::zero();
+  __syncthreads();
+  // column j of the inverse by forward substitution (thread row 0 of each column does it)
+  if (i == 0 && j < nb) {
+    for (int r = 0; r < nb; ++r) {
+      T v = (r == j) ? s::one() : s::zero();
+      for (int m = j; m < r; ++m) v = s::sub(v, s::mul(a[r][m], x[m][j]));
+      // divide by the (real, positive) diagonal
+      x[r][j] = (r < j) ? s::zero() : s::scale(v, 1.0 / s::re(a[r][r]));
+    }
+  }
+  __syncthreads();
+  if (i < nb && j < nb) Lb[i + (int64_t)j * ldl] = (j <= i) ? x[i][j] : s::zero();
+}
+
+template <typename T> __global__ void zero_upper_kernel(int k, T* G, int64_t ldg) {
+  int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i < k && j < k && i < j) G[i + (int64_t)j * ldg] = S<T>::zero();
+}
+
+template <typename T> void zero_upper(cudaStream_t st, int k, T* G, int64_t ldg) {
+  zero_upper_kernel<T><<<dim3(ceil_div(k, 32), ceil_div(k, 32)), dim3(32, 32), 0, st>>>(k, G, ldg);
+  CHASE_CHECK_LAUNCH();
+}
+
+template <typename T> void trtri_diag(cudaStream_t st, int k, T* L, int64_t ldl) {
+  trtri_diag_kernel<T><<<ceil_div(k, CB), dim3(CB, CB), 0, st>>>(k, L, ldl);
+  CHASE_CHECK_LAUNCH();
+}
+
 // ============================================================== generator
 template <typename T>
 __global__ void generate_wy_kernel(T* A, int64_t n, int64_t lda, const double* __restrict__ lam,
@@ -463,7 +503,9 @@ void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* la
   template void hermitianize<T>(cudaStream_t, int, T*, int64_t);                                                  \
   template void potrf_lower<T>(cudaStream_t, int, T*, int64_t, int*, T*, int64_t);                                \
   template void trsm_right_lh<T>(cudaStream_t, int64_t, int, T*, int64_t, const T*, int64_t, T*, int64_t);        \
-  template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int);
+  template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int); \
+  template void zero_upper<T>(cudaStream_t, int, T*, int64_t);                                                    \
+  template void trtri_diag<T>(cudaStream_t, int, T*, int64_t);
 INST(double)
 INST(double2)
 #undef INST

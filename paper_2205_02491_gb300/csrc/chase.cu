@@ -195,6 +195,42 @@ template <typename T> struct Solver {
     }
   }
 
+  // C = op(A) op(B) with FP64 accuracy: split tensor-core products for large shapes, DFMA for
+  // small ones (and always in the native mode).  Split products may write C over an operand.
+  bool use_split(int mode, int64_t M, int64_t N, int64_t K) {
+    if (mode == CHASE_FP64_NATIVE || !oz::available()) return false;
+    double mflop = (S<T>::cplx ? 8.0 : 2.0) * (double)M * (double)N * (double)K * 1e-6;
+    return mflop >= (double)c->opts.native_below_mflop;
+  }
+  void gemm(Op opA, const T* A, int64_t lda, Op opB, const T* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
+            const Epi& e, int mode) {
+    if (use_split(mode, M, N, K))
+      oz::gemm<T>(st(), c->ozw, opA, A, lda, opB, B, ldb, M, N, K, e, CHASE_FP64);
+    else
+      gemm_f64<T>(st(), opA, opB, M, N, K, A, lda, B, ldb, e, W(), c->work_elems);
+  }
+
+  // L (k x k lower, diagonal CB-blocks already inverted) -> L^{-1} by recursive halving:
+  // [[A, 0], [B, C]]^{-1} = [[A^-1, 0], [-C^-1 B A^-1, C^-1]].  tmp: k*k/4 scalars.
+  void trtri_combine(T* L, int64_t ld, int k, T* tmp, int mode) {
+    if (k <= 32) return;
+    int k1 = ((k / 2 + 31) / 32) * 32;
+    if (k1 >= k) k1 = k - 32;
+    const int k2 = k - k1;
+    trtri_combine(L, ld, k1, tmp, mode);
+    trtri_combine(L + k1 + (int64_t)k1 * ld, ld, k2, tmp, mode);
+    T* B = L + k1;
+    Epi e1;
+    e1.C = tmp;
+    e1.ldc = k2;
+    gemm(OP_N, B, ld, OP_N, L, ld, k2, k1, k1, e1, mode);  // tmp = B A^-1
+    Epi e2;
+    e2.C = B;
+    e2.ldc = ld;
+    e2.alpha = -1.0;
+    gemm(OP_N, L + k1 + (int64_t)k1 * ld, ld, OP_N, tmp, k2, k2, k1, k2, e2, mode);  // B = -C^-1 tmp
+  }
+
   // ------------------------------------------------------------ Algorithm 1, line 4
   // Filter the k columns of Y0 (ld n) in place; T1 (ld n) is the ping-pong partner.
   // deg_host non-decreasing; deg_dev the same on the device.
@@ -238,16 +274,17 @@ template <typename T> struct Solver {
 
   // ------------------------------------------------------------ Algorithm 1, line 5
   // X (n x k, ld ldx) <- orthonormal basis of span(X) orthogonal to Y (n x l, ld ldy, orthonormal).
-  void qr(const T* Y, int64_t ldy, int l, T* X, int64_t ldx, int64_t n, int k) {
+  void qr(const T* Y, int64_t ldy, int l, T* X, int64_t ldx, int64_t n, int k, int qr_mode) {
     if (k <= 0) return;
     T* Gm = Gb();
     // one block classical Gram-Schmidt pass against the locked columns: X -= Y (Y^H X)
+    const int pm = qr_mode;
     auto project = [&]() {
       if (l <= 0) return;
       Epi e;
       e.C = Gm;
       e.ldc = l;
-      gemm_f64<T>(st(), OP_C, OP_N, l, k, n, Y, ldy, X, ldx, e, W(), c->work_elems);
+      gemm(OP_C, Y, ldy, OP_N, X, ldx, l, k, n, e, pm);
       Epi u;
       u.C = X;
       u.ldc = ldx;
@@ -255,7 +292,7 @@ template <typename T> struct Solver {
       u.Z = X;
       u.ldz = ldx;
       u.beta = 1.0;
-      gemm_f64<T>(st(), OP_N, OP_N, n, k, l, Y, ldy, Gm, l, u, W(), c->work_elems);
+      gemm(OP_N, Y, ldy, OP_N, Gm, l, n, k, l, u, pm);
     };
     project();
     // column equilibration (does not change the span)
@@ -265,7 +302,7 @@ template <typename T> struct Solver {
       Epi e;
       e.C = Gm;
       e.ldc = k;
-      gemm_f64<T>(st(), OP_C, OP_N, k, k, n, X, ldx, X, ldx, e, W(), c->work_elems);
+      gemm(OP_C, X, ldx, OP_N, X, ldx, k, k, n, e, pm);
       hermitianize<T>(st(), k, Gm, k);
       if (shift_factor > 0.0) {
         fro_norm2<T>(st(), n, k, X, ldx, c->dwork);
@@ -281,7 +318,18 @@ template <typename T> struct Solver {
       CHASE_CUDA(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, st()));
       CHASE_CUDA(cudaStreamSynchronize(st()));
       if (info != 0) return false;
-      trsm_right_lh<T>(st(), n, k, X, ldx, Gm, k, W(), c->work_elems);
+      if (use_split(pm, n, k, k)) {
+        // X <- X L^{-H} as one product with the explicit triangular inverse (written over X)
+        zero_upper<T>(st(), k, Gm, k);
+        trtri_diag<T>(st(), k, Gm, k);
+        trtri_combine(Gm, k, k, Zb(), pm);
+        Epi q;
+        q.C = X;
+        q.ldc = ldx;
+        gemm(OP_N, X, ldx, OP_C, Gm, k, n, k, k, q, pm);
+      } else {
+        trsm_right_lh<T>(st(), n, k, X, ldx, Gm, k, W(), c->work_elems);
+      }
       return true;
     };
     // Cholesky-QR2 with a projection before each pass, so the final basis is orthogonal to the
@@ -323,14 +371,14 @@ template <typename T> struct Solver {
     Epi g;
     g.C = Gb();
     g.ldc = k;
-    gemm_f64<T>(st(), OP_C, OP_N, k, k, n, Q, n, Wb, n, g, W(), c->work_elems);  // G = Q^H W
+    gemm(OP_C, Q, n, OP_N, Wb, n, k, k, n, g, rmode);  // G = Q^H W
     hermitianize<T>(st(), k, Gb(), k);
     T* jw = (T*)c->work;  // Jacobi workspace (k*k + 3k + 8 scalars)
     heev_jacobi<T>(st(), k, Gb(), k, ritz, Zb(), k, jw, c->work_elems, c->dwork, c->iwork, 1e-14, 60);
     Epi v;
     v.C = Tv;
     v.ldc = n;
-    gemm_f64<T>(st(), OP_N, OP_N, n, k, k, Q, n, Zb(), k, v, W(), c->work_elems);  // Vhat = Q Z
+    gemm(OP_N, Q, n, OP_N, Zb(), k, n, k, k, v, rmode);  // Vhat = Q Z
     Epi r;
     r.C = Q;
     r.ldc = n;
@@ -338,7 +386,7 @@ template <typename T> struct Solver {
     r.ldy = n;
     r.gamma = -1.0;
     r.ycol = ritz;
-    gemm_f64<T>(st(), OP_N, OP_N, n, k, k, Wb, n, Zb(), k, r, W(), c->work_elems);  // R = W Z - Vhat diag(ritz)
+    gemm(OP_N, Wb, n, OP_N, Zb(), k, n, k, k, r, rmode);  // R = W Z - Vhat diag(ritz)
     colnorms<T>(st(), n, k, Q, n, res);
     copy_cols<T>(st(), n, k, Tv, n, Q, n);
   }
@@ -424,7 +472,7 @@ template <typename T> struct Solver {
       }
       {
         Timer t(c, 1, &S.ms_qr);
-        qr(V(), n, l, Vact, n, n, k);
+        qr(V(), n, l, Vact, n, n, k, mode == CHASE_FP64_NATIVE ? CHASE_FP64_NATIVE : CHASE_FP64);
         t.stop();
       }
       {
@@ -565,6 +613,7 @@ void chase_default_opts(chase_opts* o) {
   o->extra_deg = 2;
   o->nfinal = 1;
   o->oz_slices = 7;
+  o->native_below_mflop = 2000;
 }
 
 static int64_t lanczos_elems(int64_t n, int runs, int steps) {
@@ -600,7 +649,7 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
   chase_default_opts(&c->opts);
   if (opts) c->opts = *opts;
   if (c->opts.maxdeg < 1 || c->opts.lanczos_runs < 1 || c->opts.lanczos_runs > 8 || c->opts.lanczos_steps < 1 ||
-      c->opts.lanczos_steps > 64 || c->opts.maxiter < 1 || c->opts.oz_slices < 2 || c->opts.oz_slices > 8) {
+      c->opts.lanczos_steps > 64 || c->opts.maxiter < 1 || c->opts.oz_slices < 6 || c->opts.oz_slices > 7 || c->opts.native_below_mflop < 0) {
     delete c;
     return CHASE_ERR_ARG;
   }
@@ -751,10 +800,10 @@ chase_status chase_qr(chase_ctx* c, void* X, int64_t n, int64_t ldx, int ncols, 
                 CHASE_ERR_ARG, "bad args");
   if (c->dtype == CHASE_C128) {
     double2* x = (double2*)X;
-    Solver<double2>(c).qr(x, ldx, nlocked, x + nlocked * ldx, ldx, n, ncols - nlocked);
+    Solver<double2>(c).qr(x, ldx, nlocked, x + nlocked * ldx, ldx, n, ncols - nlocked, CHASE_FP64);
   } else {
     double* x = (double*)X;
-    Solver<double>(c).qr(x, ldx, nlocked, x + nlocked * ldx, ldx, n, ncols - nlocked);
+    Solver<double>(c).qr(x, ldx, nlocked, x + nlocked * ldx, ldx, n, ncols - nlocked, CHASE_FP64);
   }
   CHASE_CUDA(cudaStreamSynchronize(c->stream));
   API_END(c)

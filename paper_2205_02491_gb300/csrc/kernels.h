@@ -41,6 +41,9 @@ void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, 
 template <typename T>
 void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T* L, int64_t ldl, T* work,
                    int64_t work_elems);
+template <typename T> void zero_upper(cudaStream_t st, int k, T* G, int64_t ldg);
+// inverts every CB x CB diagonal block of the lower-triangular L in place (CB = 32)
+template <typename T> void trtri_diag(cudaStream_t st, int k, T* L, int64_t ldl);
 template <typename T> void add_diag(cudaStream_t st, int k, T* G, int64_t ldg, const double* shift_dev, double shift);
 template <typename T> void hermitianize(cudaStream_t st, int k, T* G, int64_t ldg);
 template <typename T> void fro_norm2(cudaStream_t st, int64_t n, int k, const T* X, int64_t ldx, double* out);

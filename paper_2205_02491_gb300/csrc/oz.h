@@ -17,7 +17,9 @@ struct Workspace {
   int ne_max = 0;
   void* a_planes = nullptr;   // bf16 digit planes of A
   void* b_planes = nullptr;   // bf16 digit planes of the right operand
+  void* l_planes = nullptr;   // bf16 digit planes of a general left operand
   double* a_scale = nullptr;  // per-row power-of-two scale of A
+  double* l_scale = nullptr;  // per-row scale of the general left operand
   double* b_scale = nullptr;  // per-column scale of the right operand
   int* flags = nullptr;       // device error flags of the bounded waits
   const void* a_src = nullptr;  // A whose planes are cached
@@ -36,6 +38,11 @@ void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda
 template <typename T>
 void hemm(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, const T* B, int64_t ldb, int k,
           const Epi& e, int mode);
+// C = op(A) op(B) (M x N, inner K) through split products; op(A) = A (M x K) or A^H (A: K x M),
+// op(B) = B (K x N) or B^H (B: N x K).
+template <typename T>
+void gemm(cudaStream_t st, Workspace& w, Op opA, const T* A, int64_t lda, Op opB, const T* B, int64_t ldb, int64_t M,
+          int64_t N, int64_t K, const Epi& e, int mode);
 
 }  // namespace oz
 }  // namespace chase

@@ -563,6 +563,59 @@ __global__ void split_cols_kernel(int64_t K, int64_t Kpad, int ncols, const T* _
   }
 }
 
+// Per-row power-of-two scale of a column-major X (vector i = row i, K along columns).
+template <typename T>
+__global__ void row_scale_kernel(int64_t nvec, int64_t K, const T* __restrict__ X, int64_t ldx, double* scale) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nvec) return;
+  double m = 0.0;
+  for (int64_t kk = 0; kk < K; ++kk) {
+    T v = X[i + kk * ldx];
+    m = fmax(m, fmax(fabs(S<T>::re(v)), fabs(S<T>::im(v))));
+  }
+  int e = 0;
+  if (m > 0.0 && isfinite(m)) frexp(m, &e);
+  scale[i] = m > 0.0 ? ldexp(1.0, e) : 1.0;
+}
+
+// Planes of the vectors i = rows of X (K along columns), via a 32x32 shared-memory transpose.
+template <typename T, int NS, int KIND>
+__global__ void split_rows_kernel(int64_t nvec, int64_t K, int64_t Kpad, const T* __restrict__ X, int64_t ldx,
+                                  const double* __restrict__ scale, int conj, __nv_bfloat16* planes) {
+  constexpr bool CPLX = S<T>::cplx;
+  __shared__ T tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int64_t kk = k0 + r, i = i0 + threadIdx.x;
+    tile[r][threadIdx.x] = (kk < K && i < nvec) ? X[i + kk * ldx] : S<T>::zero();
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int64_t i = i0 + r, kk = k0 + threadIdx.x;
+    if (i >= nvec || kk >= K) continue;
+    T v = tile[threadIdx.x][r];
+    const double inv = 1.0 / scale[i];
+    double re = S<T>::re(v) * inv;
+    double im = (conj ? -S<T>::im(v) : S<T>::im(v)) * inv;
+    __nv_bfloat16 dr[NS], di[NS];
+    digits<NS>(re, dr);
+    if (CPLX) digits<NS>(im, di);
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      if (!CPLX) {
+        planes[((int64_t)t * nvec + i) * Kpad + kk] = dr[t];
+      } else if (KIND == 0) {
+        planes[((int64_t)(t * 2 + 0) * nvec + i) * Kpad + kk] = dr[t];
+        planes[((int64_t)(t * 2 + 1) * nvec + i) * Kpad + kk] = di[t];
+      } else {
+        planes[((int64_t)(t * 3 + 0) * nvec + i) * Kpad + kk] = __hneg(di[t]);
+        planes[((int64_t)(t * 3 + 1) * nvec + i) * Kpad + kk] = dr[t];
+        planes[((int64_t)(t * 3 + 2) * nvec + i) * Kpad + kk] = di[t];
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------- host side
 typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                              const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -616,12 +669,17 @@ bool available() {
   return ok == 1;
 }
 
+static int64_t left_elems(int64_t n_max, int ne_max) {
+  return std::max<int64_t>(n_max * kpad(ne_max), (int64_t)ne_max * kpad(n_max));
+}
+
 int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices) {
   int ap = complex_ ? 2 : 1, bp = complex_ ? 3 : 1;
   int64_t kp = kpad(n_max);
   int64_t a = (int64_t)slices * ap * n_max * kp * 2;
+  int64_t l = (int64_t)slices * ap * left_elems(n_max, ne_max) * 2;
   int64_t b = (int64_t)slices * bp * ne_max * kp * 2;
-  return a + b + (n_max + ne_max) * 8 + 64;
+  return a + l + b + (2 * n_max + 2 * ne_max) * 8 + 64;
 }
 
 void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices) {
@@ -633,8 +691,10 @@ void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices) 
   int ap = complex_ ? 2 : 1, bp = complex_ ? 3 : 1;
   int64_t kp = kpad(n_max);
   CHASE_CUDA(cudaMalloc(&w.a_planes, (size_t)slices * ap * n_max * kp * 2));
+  CHASE_CUDA(cudaMalloc(&w.l_planes, (size_t)slices * ap * left_elems(n_max, ne_max) * 2));
   CHASE_CUDA(cudaMalloc(&w.b_planes, (size_t)slices * bp * ne_max * kp * 2));
   CHASE_CUDA(cudaMalloc(&w.a_scale, n_max * sizeof(double)));
+  CHASE_CUDA(cudaMalloc(&w.l_scale, std::max<int64_t>(n_max, ne_max) * sizeof(double)));
   CHASE_CUDA(cudaMalloc(&w.b_scale, ne_max * sizeof(double)));
   CHASE_CUDA(cudaMalloc(&w.flags, 16 * sizeof(int)));
   CHASE_CUDA(cudaMemset(w.flags, 0, 16 * sizeof(int)));
@@ -642,10 +702,52 @@ void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices) 
 }
 
 void destroy(Workspace& w) {
-  void* ps[] = {w.a_planes, w.b_planes, w.a_scale, w.b_scale, w.flags};
+  void* ps[] = {w.a_planes, w.l_planes, w.b_planes, w.a_scale, w.l_scale, w.b_scale, w.flags};
   for (void* p : ps)
     if (p) cudaFree(p);
   w = Workspace{};
+}
+
+// Split nvec vectors of length K taken from a column-major X: by columns (vector = column,
+// optionally conjugated) or by rows (vector = row).  kind 0: left-operand planes (re, im);
+// kind 1: right-operand planes (-im, re, im).
+template <typename T>
+static void split(cudaStream_t st, int S_, int kind, bool by_rows, bool conj, const T* X, int64_t ld, int64_t nvec,
+                  int64_t K, void* planes, double* scale) {
+  const int64_t kp = kpad(K);
+  if (!by_rows) {
+    col_scale_kernel<T><<<(unsigned)nvec, 256, 0, st>>>(K, X, ld, scale);
+    CHASE_CHECK_LAUNCH();
+    dim3 grid(std::min<unsigned>(ceil_div(K, 256), 32), (unsigned)nvec);
+#define SC(SS, KD) split_cols_kernel<T, SS, KD><<<grid, 256, 0, st>>>(K, kp, (int)nvec, X, ld, scale, conj ? 1 : 0, (__nv_bfloat16*)planes)
+#define SWK(SS) if (kind == 0) SC(SS, 0); else SC(SS, 1);
+    switch (S_) {
+      case 2: SWK(2); break;
+      case 3: SWK(3); break;
+      case 6: SWK(6); break;
+      case 7: SWK(7); break;
+      default: CHASE_REQUIRE(false, 1, "unsupported slice count");
+    }
+#undef SWK
+#undef SC
+  } else {
+    row_scale_kernel<T><<<ceil_div(nvec, 128), 128, 0, st>>>(nvec, K, X, ld, scale);
+    CHASE_CHECK_LAUNCH();
+    dim3 grid(ceil_div(K, 32), ceil_div(nvec, 32));
+    CHASE_REQUIRE(grid.y <= 65535, 1, "split: too many vectors");
+#define SR(SS, KD) split_rows_kernel<T, SS, KD><<<grid, dim3(32, 8), 0, st>>>(nvec, K, kp, X, ld, scale, conj ? 1 : 0, (__nv_bfloat16*)planes)
+#define SWK(SS) if (kind == 0) SR(SS, 0); else SR(SS, 1);
+    switch (S_) {
+      case 2: SWK(2); break;
+      case 3: SWK(3); break;
+      case 6: SWK(6); break;
+      case 7: SWK(7); break;
+      default: CHASE_REQUIRE(false, 1, "unsupported slice count");
+    }
+#undef SWK
+#undef SR
+  }
+  CHASE_CHECK_LAUNCH();
 }
 
 template <typename T>
@@ -654,20 +756,8 @@ void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda
   // planes of all slices are nested: the S-slice split's first slices are the 2- and 3-slice splits
   if (w.a_src == (const void*)A && w.a_n == n && w.a_mode == w.slices) return;
   (void)mode;
-  const int S_ = w.slices;
-  int64_t kp = kpad(n);
-  col_scale_kernel<T><<<(unsigned)n, 256, 0, st>>>(n, A, lda, w.a_scale);
-  CHASE_CHECK_LAUNCH();
-  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 32), (unsigned)n);
   // A Hermitian: K-major row i of A = conjugate of column i of its column-major storage
-#define SPLIT(SS) split_cols_kernel<T, SS, 0><<<grid, 256, 0, st>>>(n, kp, (int)n, A, lda, w.a_scale, 1, (__nv_bfloat16*)w.a_planes)
-  switch (S_) {
-    case 6: SPLIT(6); break;
-    case 7: SPLIT(7); break;
-    default: CHASE_REQUIRE(false, 1, "oz_slices must be 6 or 7");
-  }
-#undef SPLIT
-  CHASE_CHECK_LAUNCH();
+  split<T>(st, w.slices, 0, false, true, A, lda, n, n, w.a_planes, w.a_scale);
   w.a_src = A;
   w.a_n = n;
   w.a_mode = w.slices;
@@ -680,14 +770,16 @@ void invalidate(Workspace& w) {
   if (w.flags) CHASE_CUDA(cudaMemset(w.flags, 0, 16 * sizeof(int)));  // a new call starts clean
 }
 
+// C(M x N) = L(M x K) R(K x N) from digit planes (left: rows = M vectors of length K, right:
+// rows = N vectors of length K), split with l_slices_total / S slices respectively.
 template <int S, int NEX, bool CPLX>
-static void launch(cudaStream_t st, Workspace& w, int64_t n, int k, int a_slices, const Epi& e) {
+static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double* lsc, int l_slices_total,
+                   const void* rpl, const double* rsc, int64_t M, int64_t N, int64_t K, const Epi& e) {
   using Cf = Cfg<S, NEX, CPLX>;
-  int64_t kp = kpad(n);
+  const int64_t kp = kpad(K);
   const int ap = CPLX ? 2 : 1, bp = CPLX ? 3 : 1;
-  // A planes were split with w.slices slices: only the first S are read (nested digits)
-  CUtensorMap ma = make_map(w.a_planes, n, kp, n, a_slices * ap, BM);
-  CUtensorMap mb = make_map(w.b_planes, n, kp, k, S * bp, Cf::BROWS);
+  CUtensorMap ma = make_map(lpl, K, kp, M, l_slices_total * ap, BM);
+  CUtensorMap mb = make_map(rpl, K, kp, N, S * bp, Cf::BROWS);
   static bool attr_set = false;
   if (!attr_set) {
     CHASE_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -695,10 +787,21 @@ static void launch(cudaStream_t st, Workspace& w, int64_t n, int k, int a_slices
     attr_set = true;
   }
   EpiArgs ea{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
-  dim3 grid(ceil_div(k, Cf::NCOLS), ceil_div(n, BM));
-  oz_gemm_kernel<S, NEX, CPLX><<<grid, NTHREADS, Cf::SMEM_BYTES, st>>>(ma, mb, (int)n, k, (int)n, w.a_scale,
-                                                                         w.b_scale, ea, w.flags);
+  dim3 grid(ceil_div(N, Cf::NCOLS), ceil_div(M, BM));
+  CHASE_REQUIRE(grid.y <= 65535, 1, "split product: M too large");
+  oz_gemm_kernel<S, NEX, CPLX><<<grid, NTHREADS, Cf::SMEM_BYTES, st>>>(ma, mb, (int)M, (int)N, (int)K, lsc, rsc, ea,
+                                                                         w.flags);
   CHASE_CHECK_LAUNCH();
+}
+
+template <bool CPLX>
+static void dispatch(cudaStream_t st, Workspace& w, int S_, const void* lpl, const double* lsc, int l_slices_total,
+                     int64_t M, int64_t N, int64_t K, const Epi& e) {
+  CHASE_REQUIRE(K <= 65472, 1, "split products support K <= 65472 (int64 exact-level sums)");
+  if (S_ == 7) launch<7, 5, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  else if (S_ == 6) launch<6, 5, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  else if (S_ == 3) launch<3, 0, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  else launch<2, 0, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
 }
 
 template <typename T>
@@ -707,27 +810,24 @@ void hemm(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, con
   CHASE_REQUIRE(w.ready, 9, "split products not initialised");
   CHASE_REQUIRE(w.a_src == (const void*)A && w.a_n == n, 7, "prepare_A must precede hemm");
   CHASE_REQUIRE(k <= w.ne_max && n <= w.n_max, 1, "hemm size exceeds the workspace");
-  CHASE_REQUIRE(n <= 65472, 1, "split products support K <= 65472 (int64 exact-level sums)");
-  constexpr bool CPLX = S<T>::cplx;
   const int S_ = slices_for(mode, w.slices);
-  int64_t kp = kpad(n);
-  col_scale_kernel<T><<<(unsigned)k, 256, 0, st>>>(n, B, ldb, w.b_scale);
-  CHASE_CHECK_LAUNCH();
-  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 32), (unsigned)k);
-#define SPLITB(SS) split_cols_kernel<T, SS, 1><<<grid, 256, 0, st>>>(n, kp, k, B, ldb, w.b_scale, 0, (__nv_bfloat16*)w.b_planes)
-  switch (S_) {
-    case 2: SPLITB(2); break;
-    case 3: SPLITB(3); break;
-    case 6: SPLITB(6); break;
-    case 7: SPLITB(7); break;
-    default: CHASE_REQUIRE(false, 1, "unsupported slice count");
-  }
-#undef SPLITB
-  CHASE_CHECK_LAUNCH();
-  if (S_ == 7) launch<7, 5, CPLX>(st, w, n, k, w.slices, e);
-  else if (S_ == 6) launch<6, 5, CPLX>(st, w, n, k, w.slices, e);
-  else if (S_ == 3) launch<3, 0, CPLX>(st, w, n, k, w.slices, e);
-  else launch<2, 0, CPLX>(st, w, n, k, w.slices, e);
+  split<T>(st, S_, 1, false, false, B, ldb, k, n, w.b_planes, w.b_scale);
+  dispatch<S<T>::cplx>(st, w, S_, w.a_planes, w.a_scale, w.slices, n, k, n, e);
+}
+
+template <typename T>
+void gemm(cudaStream_t st, Workspace& w, Op opA, const T* A, int64_t lda, Op opB, const T* B, int64_t ldb, int64_t M,
+          int64_t N, int64_t K, const Epi& e, int mode) {
+  CHASE_REQUIRE(w.ready, 9, "split products not initialised");
+  if (M <= 0 || N <= 0) return;
+  CHASE_REQUIRE(N <= w.ne_max && M * kpad(K) <= left_elems(w.n_max, w.ne_max) && N * kpad(K) <= (int64_t)w.ne_max * kpad(w.n_max),
+                1, "split product exceeds the workspace");
+  const int S_ = slices_for(mode, w.slices);
+  // left operand: OP_N rows of A (M x K), OP_C conjugated columns of A (K x M)
+  split<T>(st, S_, 0, opA == OP_N, opA == OP_C, A, lda, M, K, w.l_planes, w.l_scale);
+  // right operand: OP_N columns of B (K x N), OP_C conjugated rows of B (N x K)
+  split<T>(st, S_, 1, opB == OP_C, opB == OP_C, B, ldb, N, K, w.b_planes, w.b_scale);
+  dispatch<S<T>::cplx>(st, w, S_, w.l_planes, w.l_scale, S_, M, N, K, e);
 }
 
 int read_flags(cudaStream_t st, Workspace& w) {
@@ -742,6 +842,10 @@ template void prepare_A<double>(cudaStream_t, Workspace&, const double*, int64_t
 template void prepare_A<double2>(cudaStream_t, Workspace&, const double2*, int64_t, int64_t, int);
 template void hemm<double>(cudaStream_t, Workspace&, const double*, int64_t, int64_t, const double*, int64_t, int,
                            const Epi&, int);
+template void gemm<double>(cudaStream_t, Workspace&, Op, const double*, int64_t, Op, const double*, int64_t, int64_t,
+                           int64_t, int64_t, const Epi&, int);
+template void gemm<double2>(cudaStream_t, Workspace&, Op, const double2*, int64_t, Op, const double2*, int64_t, int64_t,
+                            int64_t, int64_t, const Epi&, int);
 template void hemm<double2>(cudaStream_t, Workspace&, const double2*, int64_t, int64_t, const double2*, int64_t, int,
                             const Epi&, int);
 

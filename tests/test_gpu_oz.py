@@ -134,3 +134,52 @@ def test_solve_c1_modes(pkg, mode):
     assert subspace_sin(E, V) <= max(1e-8, 1.01 * np.linalg.norm(R) / gap)
     if mode != "fp64":
         assert st["lowp_iterations"] >= 1
+
+
+SPLIT_ALL = {"native_below_mflop": 0}
+
+
+def test_qr_split_products(pkg):
+    n, k, l = 700, 48, 9
+    g = np.random.default_rng(19)
+    Y, _ = np.linalg.qr(g.standard_normal((n, l)) + 1j * g.standard_normal((n, l)))
+    X = g.standard_normal((n, k - l)) + 1j * g.standard_normal((n, k - l))
+    X[:, 5] = X[:, 4] + 1e-6 * X[:, 5]
+    s = pkg.Chase(n, k, complex_=True, opts=SPLIT_ALL)
+    Xt = dev(np.concatenate([Y, X], axis=1))
+    s.qr(Xt, nlocked=l)
+    Q = host(Xt)
+    assert np.array_equal(Q[:, :l], Y)
+    assert np.max(np.abs(np.conj(Q.T) @ Q - np.eye(k))) <= 1e-12
+    assert subspace_sin(Q, O.qr_step(Y, X)) <= 1e-6
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_rayleigh_ritz_split_products(pkg, cplx):
+    n, k = 600, 40
+    p = G.problem_small(n, 20, 20, complex_=cplx, seed_pid=21)
+    A = p.dense()
+    Q, _ = np.linalg.qr(p.V0[:, :k])
+    wo, Vo = O.rayleigh_ritz(A, Q)
+    ro = O.residuals(A, Vo, wo)
+    s = pkg.Chase(n, k, complex_=cplx, opts=SPLIT_ALL)
+    Qt = dev(Q)
+    w, r = s.rayleigh_ritz(dev(A), Qt)
+    V = host(Qt)
+    assert np.max(np.abs(w - wo)) <= 1e-12
+    assert np.max(np.abs(r - ro)) <= 1e-11
+    assert np.max(np.abs(np.conj(V.T) @ V - np.eye(k))) <= 1e-12
+
+
+@pytest.mark.parametrize("mode", ["fp64", "bf16x6"])
+def test_solve_c1_all_split_products(pkg, mode):
+    p = G.problem_c1()
+    A = p.dense()
+    s = pkg.Chase(p.n, p.ne, complex_=True, opts=SPLIT_ALL)
+    w, Vt = s.solve(dev(A), p.nev, p.nex, p.tol, p.deg, mode, dev(p.V0), dev(p.L0))
+    w = w.cpu().numpy()
+    V = host(Vt)
+    nrm = p.norm2()
+    assert np.max(np.abs(w - p.lam[:p.nev])) <= 1e-10 * nrm
+    R = G.implicit_matvec(p.lam, p.U, V) - V * w[None, :]
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
