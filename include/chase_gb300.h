@@ -82,7 +82,13 @@ typedef struct {
   double max_resid;    /* largest relative residual among the returned pairs */
   int qr_fallbacks;    /* shifted Cholesky-QR fallbacks taken */
   int filter_launches; /* filter product launches */
+  double ms_filter_kernel;      /* CUDA-event time of the FP64 split-product filter kernels alone */
+  int filter_kernel_launches;   /* launches timed in ms_filter_kernel */
+  double ms_filter_kernel_lowp; /* same for the mixed-precision bulk filter kernels */
 } chase_stats_t;
+
+/* Kernel launches made by this library in this process so far (all contexts). */
+int64_t chase_kernel_launch_count(void);
 
 /* Fill *opts with defaults. */
 void chase_default_opts(chase_opts* opts);

@@ -258,6 +258,20 @@ def chebyshev_filter(A: np.ndarray, V: np.ndarray, m: np.ndarray, b_sup: float, 
     return out, int(m.sum())
 
 
+def chebyshev_step_rows(A_rows: np.ndarray, rows: np.ndarray, Y: np.ndarray, Y_prev_rows: np.ndarray, s: int,
+                        c: float, alpha: np.ndarray, beta: np.ndarray) -> np.ndarray:
+    """Step s of the three-term recurrence restricted to a block of rows of A (Eq. three-terms-recurrence).
+
+    Returns rows `rows` of Y_s = alpha_s (A - cI) Y_{s-1} + beta_s Y_{s-2}, given those rows of A
+    (A_rows), the full Y_{s-1} (Y) and the same rows of Y_{s-2}.  Used to time a bounded sample of
+    the filter on the CPU.
+    """
+    out = alpha[s] * (A_rows @ Y - c * Y[rows, :])
+    if s > 1:
+        out += beta[s] * Y_prev_rows
+    return out
+
+
 def chebyshev_scalar(x, m: int, b_sup: float, mu_1: float, mu_ne: float):
     """p_m(x) = C_m((x - c)/e) / C_m((mu_1 - c)/e), the scalar the filter applies to an eigenvalue x."""
     c = 0.5 * (b_sup + mu_ne)

@@ -21,7 +21,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_NOCONV", 4: "ERR_QR_BREAK
 # every symbol include/chase_gb300.h declares
 EXPORTED = ["chase_default_opts", "chase_create", "chase_destroy", "chase_last_error", "chase_workspace_bytes",
             "chase_solve", "chase_solve_batched", "chase_eigvals", "chase_eigvecs", "chase_stats", "chase_backward",
-            "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_heevj", "chase_hemm",
+            "chase_kernel_launch_count", "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_heevj", "chase_hemm",
             "chase_generate"]
 
 
@@ -36,7 +36,9 @@ class Stats(C.Structure):
                 ("lowp_iterations", C.c_int), ("ms_total", C.c_double), ("ms_lanczos", C.c_double),
                 ("ms_filter", C.c_double), ("ms_qr", C.c_double), ("ms_rr", C.c_double), ("ms_resid", C.c_double),
                 ("b_sup", C.c_double), ("mu_1", C.c_double), ("mu_ne", C.c_double), ("norm_est", C.c_double),
-                ("max_resid", C.c_double), ("qr_fallbacks", C.c_int), ("filter_launches", C.c_int)]
+                ("max_resid", C.c_double), ("qr_fallbacks", C.c_int), ("filter_launches", C.c_int),
+                ("ms_filter_kernel", C.c_double), ("filter_kernel_launches", C.c_int),
+                ("ms_filter_kernel_lowp", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,6 +68,7 @@ def load() -> C.CDLL:
         "chase_destroy": (None, [P]),
         "chase_last_error": (C.c_char_p, [P]),
         "chase_workspace_bytes": (I64, [I64, I, I, C.POINTER(Opts)]),
+        "chase_kernel_launch_count": (I64, []),
         "chase_solve": (I, [P, P, I64, I64, I, I, D, I, I, P, P]),
         "chase_solve_batched": (I, [P, I, P, P, P, P, D, I, I, P, P, P, P]),
         "chase_eigvals": (I, [P, P, I]),

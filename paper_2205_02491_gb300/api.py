@@ -167,6 +167,11 @@ class Chase:
         return At
 
 
+def kernel_launch_count() -> int:
+    """Kernel launches made by the library in this process so far."""
+    return int(L.load().chase_kernel_launch_count())
+
+
 def workspace_bytes(n_max: int, ne_max: int, complex_: bool = True, opts: dict | None = None) -> int:
     lib = L.load()
     o = L.Opts()

@@ -25,6 +25,10 @@
 
 using namespace chase;
 
+namespace chase {
+std::atomic<long long> g_kernel_launches{0};
+}
+
 struct chase_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -462,7 +466,18 @@ template <typename T> struct Solver {
       int fmode = (mode == CHASE_FP64_NATIVE) ? CHASE_FP64_NATIVE : (lowp ? mode : CHASE_FP64);
       {
         Timer t(c, 1, &S.ms_filter);
+        if (oz::available()) oz::timing_begin(c->ozw);
         int64_t mv = filter(A, n, lda, Vact, T1act, k, m.data(), c->deg, b_sup, mu_1, mu_ne, fmode);
+        if (oz::available()) {
+          int nl = 0;
+          double ms = oz::timing_collect(c->ozw, &nl);
+          if (lowp) {
+            S.ms_filter_kernel_lowp += ms;
+          } else {
+            S.ms_filter_kernel += ms;
+            S.filter_kernel_launches += nl;
+          }
+        }
         S.matvecs += mv;
         if (lowp) {
           S.matvecs_lowp += mv;
@@ -721,6 +736,8 @@ void chase_destroy(chase_ctx* c) {
 }
 
 const char* chase_last_error(const chase_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t chase_kernel_launch_count(void) { return (int64_t)chase::g_kernel_launches.load(); }
 
 chase_status chase_solve(chase_ctx* c, const void* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg,
                          int mode, const void* V0, const void* L0) {

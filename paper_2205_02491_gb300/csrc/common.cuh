@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <string>
 
 namespace chase {
@@ -74,7 +75,13 @@ struct Error {
       throw ::chase::Error{6, std::string(#call) + ": " + cudaGetErrorString(_e)};              \
   } while (0)
 
-#define CHASE_CHECK_LAUNCH() CHASE_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by CHASE_CHECK_LAUNCH(), which also counts it
+extern std::atomic<long long> g_kernel_launches;
+#define CHASE_CHECK_LAUNCH()                        \
+  do {                                              \
+    ::chase::g_kernel_launches.fetch_add(1);        \
+    CHASE_CUDA(cudaGetLastError());                 \
+  } while (0)
 
 #define CHASE_REQUIRE(cond, code, text)                                                          \
   do {                                                                                           \

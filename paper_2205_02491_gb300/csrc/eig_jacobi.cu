@@ -215,6 +215,7 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
   bool done = false;
   for (; sweeps <= max_sweeps; ++sweeps) {
     offdiag_partial_kernel<T><<<k, 128, 0, st>>>(k, G, ldg, part);
+    CHASE_CHECK_LAUNCH();
     offdiag_sum_kernel<<<1, 32, 0, st>>>(k, part, dwork);
     CHASE_CHECK_LAUNCH();
     CHASE_CUDA(cudaMemcpyAsync(hstat, dwork, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -230,8 +231,11 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
     dim3 zgrid(ceil_div(k, 128), half);
     for (int r = 0; r < kp - 1; ++r) {
       jacobi_params_kernel<T><<<ceil_div(half, 128), 128, 0, st>>>(k, kp, r, G, ldg, rot);
+      CHASE_CHECK_LAUNCH();
       jacobi_apply_g_kernel<T><<<ggrid, gblk, 0, st>>>(k, kp, r, G, ldg, rot);
+      CHASE_CHECK_LAUNCH();
       jacobi_apply_z_kernel<T><<<zgrid, 128, 0, st>>>(k, kp, r, Zu, k, rot);
+      CHASE_CHECK_LAUNCH();
     }
     CHASE_CHECK_LAUNCH();
   }

@@ -354,17 +354,25 @@ void lanczos(cudaStream_t st, const T* A, int64_t n, int64_t lda, int ne, const 
     int m = j + 1;
     // alpha_j and the three-term update
     basis_dots_kernel<T><<<dim3(DOT_CHUNKS, runs), 256, 0, st>>>(n, m, steps, Vb, W, part);
+    CHASE_CHECK_LAUNCH();
     dots_reduce_kernel<T><<<runs, LZ_MAXS, 0, st>>>(runs, m, part, d);
+    CHASE_CHECK_LAUNCH();
     lanczos_coef3_kernel<T><<<1, 32, 0, st>>>(runs, j, d, coef, alpha, beta);
+    CHASE_CHECK_LAUNCH();
     basis_update_kernel<T><<<dim3(ceil_div(n, 256), runs), 256, 0, st>>>(n, m, steps, Vb, W, coef);
+    CHASE_CHECK_LAUNCH();
     // one full classical Gram-Schmidt pass against the run's basis
     basis_dots_kernel<T><<<dim3(DOT_CHUNKS, runs), 256, 0, st>>>(n, m, steps, Vb, W, part);
+    CHASE_CHECK_LAUNCH();
     dots_reduce_kernel<T><<<runs, LZ_MAXS, 0, st>>>(runs, m, part, d);
+    CHASE_CHECK_LAUNCH();
     basis_update_kernel<T><<<dim3(ceil_div(n, 256), runs), 256, 0, st>>>(n, m, steps, Vb, W, d);
+    CHASE_CHECK_LAUNCH();
     lanczos_norm_kernel<T><<<runs, 256, 0, st>>>(n, steps, j, W, Vb, beta);
     CHASE_CHECK_LAUNCH();
   }
   tridiag_jacobi_kernel<<<runs, LZ_MAXS, 0, st>>>(steps, alpha, beta, theta, tau2, status);
+  CHASE_CHECK_LAUNCH();
   lanczos_bounds_kernel<<<1, 32, 0, st>>>(runs, steps, n, ne, theta, tau2, beta, out4);
   CHASE_CHECK_LAUNCH();
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "kernels.h"
 
 namespace chase {
@@ -22,6 +24,10 @@ struct Workspace {
   double* l_scale = nullptr;  // per-row scale of the general left operand
   double* b_scale = nullptr;  // per-column scale of the right operand
   int* flags = nullptr;       // device error flags of the bounded waits
+  // optional CUDA-event timing of the product kernels (filter roofline)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
   const void* a_src = nullptr;  // A whose planes are cached
   int a_mode = -1;
   int64_t a_n = 0;
@@ -32,6 +38,9 @@ int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices);
 void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices);
 void destroy(Workspace& w);
 void invalidate(Workspace& w);
+// start recording event pairs around every product kernel; collect returns (ms, launches)
+void timing_begin(Workspace& w);
+double timing_collect(Workspace& w, int* launches);
 int read_flags(cudaStream_t st, Workspace& w);
 template <typename T>
 void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, int mode);

@@ -705,6 +705,7 @@ void destroy(Workspace& w) {
   void* ps[] = {w.a_planes, w.l_planes, w.b_planes, w.a_scale, w.l_scale, w.b_scale, w.flags};
   for (void* p : ps)
     if (p) cudaFree(p);
+  for (auto& e : w.ev) cudaEventDestroy(e);
   w = Workspace{};
 }
 
@@ -763,6 +764,29 @@ void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda
   w.a_mode = w.slices;
 }
 
+void timing_begin(Workspace& w) {
+  if (w.ev.empty()) {
+    w.ev.resize(256);
+    for (auto& e : w.ev) CHASE_CUDA(cudaEventCreate(&e));
+  }
+  w.ev_used = 0;
+  w.timing = true;
+}
+
+double timing_collect(Workspace& w, int* launches) {
+  double ms = 0.0;
+  for (int i = 0; i + 1 < w.ev_used; i += 2) {
+    CHASE_CUDA(cudaEventSynchronize(w.ev[i + 1]));
+    float t = 0.f;
+    CHASE_CUDA(cudaEventElapsedTime(&t, w.ev[i], w.ev[i + 1]));
+    ms += t;
+  }
+  if (launches) *launches = w.ev_used / 2;
+  w.ev_used = 0;
+  w.timing = false;
+  return ms;
+}
+
 void invalidate(Workspace& w) {
   w.a_src = nullptr;
   w.a_n = 0;
@@ -789,9 +813,15 @@ static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double*
   EpiArgs ea{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
   dim3 grid(ceil_div(N, Cf::NCOLS), ceil_div(M, BM));
   CHASE_REQUIRE(grid.y <= 65535, 1, "split product: M too large");
+  const bool timed = w.timing && w.ev_used + 2 <= (int)w.ev.size();
+  if (timed) CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used], st));
   oz_gemm_kernel<S, NEX, CPLX><<<grid, NTHREADS, Cf::SMEM_BYTES, st>>>(ma, mb, (int)M, (int)N, (int)K, lsc, rsc, ea,
                                                                          w.flags);
   CHASE_CHECK_LAUNCH();
+  if (timed) {
+    CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used + 1], st));
+    w.ev_used += 2;
+  }
 }
 
 template <bool CPLX>
