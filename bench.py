@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--nev", type=int, default=1200)
     ap.add_argument("--nex", type=int, default=400)
     ap.add_argument("--no-tts", action="store_true", help="skip the full time-to-solution solves")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -285,6 +286,8 @@ def run_ours(args):
     # residuals), which the library copies to the host once per outer iteration
     e2e = None
     try:
+        if args.no_e2e:
+            raise RuntimeError("skipped (--no-e2e)")
         A_host = torch.empty((n, n), dtype=torch.complex128, pin_memory=True)
         A_host.copy_(At)
         V0h = V0t.cpu().pin_memory()

@@ -96,8 +96,8 @@ void chase_default_opts(chase_opts* opts);
 /* Create a context on the current CUDA device.  Preallocates the whole
  * workspace for problems up to n_max x n_max with nev+nex <= ne_max (the
  * single-GPU form of Eq. GPU_mem plus split-product buffers); returns
- * CHASE_ERR_OOM early if it does not fit.  stream: a cudaStream_t or NULL for
- * a new non-blocking stream owned by the context.  opts may be NULL. */
+ * CHASE_ERR_OOM early if it does not fit.  stream: the cudaStream_t all work of
+ * the context is enqueued on; NULL is the legacy default stream.  opts may be NULL. */
 chase_status chase_create(chase_ctx** ctx, int64_t n_max, int ne_max, chase_dtype dtype,
                           const chase_opts* opts, void* stream);
 void chase_destroy(chase_ctx* ctx);

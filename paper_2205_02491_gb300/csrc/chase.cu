@@ -674,12 +674,9 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
   c->esz = dtype == CHASE_C128 ? 16 : 8;
   try {
     CHASE_CUDA(cudaGetDevice(&c->device));
-    if (stream) {
-      c->stream = (cudaStream_t)stream;
-    } else {
-      CHASE_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-      c->own_stream = true;
-    }
+    // NULL is the legacy default stream (the one a framework's default stream maps to), so work
+    // enqueued by the caller on it before a call is ordered before the call's kernels
+    c->stream = (cudaStream_t)stream;
     for (auto& e : c->ev) CHASE_CUDA(cudaEventCreate(&e));
     size_t freeb = 0, totb = 0;
     CHASE_CUDA(cudaMemGetInfo(&freeb, &totb));
