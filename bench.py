@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--nex", type=int, default=400)
     ap.add_argument("--no-tts", action="store_true", help="skip the full time-to-solution solves")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
+    ap.add_argument("--hemm-only", default=None, choices=[None, "fp64", "bf16x6", "bf16x3"],
+                    help="time only the filter product A Y (n x n times n x (nev+nex)) in the given arithmetic; "
+                         "used for kernel profiling")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -377,10 +380,43 @@ def run_ours(args):
     return 0
 
 
+def run_hemm_only(args):
+    """Repeated filter products A Y through the C ABI (profiling helper; one JSON line)."""
+    import numpy as np
+    import torch
+
+    import paper_2205_02491_gb300 as pkg
+    from gen import problems as G
+
+    p = problem(args)
+    n, ne = p.n, p.ne
+    Bw, Dw = G.wy_factors(p.lam, p.U)
+    tdev = lambda x: torch.from_numpy(np.ascontiguousarray(np.asarray(x).T)).cuda()
+    At = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    s = pkg.Chase(n, ne, complex_=True)
+    s.generate(At, torch.from_numpy(p.lam).cuda(), tdev(p.U), tdev(Bw), tdev(Dw))
+    V0t = tdev(p.V0)
+    for _ in range(args.warmup):
+        s.hemm(At, V0t, args.hemm_only)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        s.hemm(At, V0t, args.hemm_only)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"hemm_only": args.hemm_only, "n": n, "k": ne, "ms_per_call": ms,
+                      "fp64_equiv_tflops": 8.0 * n * n * ne / (ms * 1e-3) / 1e12}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.hemm_only:
+        return run_hemm_only(args)
     return run_ours(args)
 
 
