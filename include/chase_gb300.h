@@ -173,6 +173,27 @@ chase_status chase_rayleigh_ritz(chase_ctx* ctx, const void* A_dev, int64_t n, i
 chase_status chase_heevj(chase_ctx* ctx, const void* G_dev, int64_t ldg, int k, double* w_host,
                          void* Z_dev, int64_t ldz);
 
+/* Largest k accepted by chase_heevj_noalloc. */
+#define CHASE_HEEVJ_NOALLOC_KMAX 256
+
+/* chase_heevj for callers that cannot allocate device memory (a process whose
+ * device memory is already reserved by a framework's caching allocator or its
+ * own arena, or code that must not allocate because cudaMalloc can fail under
+ * memory pressure and synchronises the device).  The paper has no counterpart:
+ * this is a deployment variant of the Rayleigh-Ritz eigensolve.
+ * Needs no context.  G_dev: k x k Hermitian (ld ldg) of type dtype, read only;
+ * eigenvalues ascending to w_host (k doubles); eigenvectors to Z_dev (k x k,
+ * ld ldz).  All work is enqueued on `stream` (NULL: legacy default stream) and
+ * the call returns when it has finished.
+ * Scratch is one fixed array in the library's device memory (about 2.1 MB per
+ * device, held until the process exits): k > CHASE_HEEVJ_NOALLOC_KMAX returns
+ * CHASE_ERR_ARG; calls that overlap on the GPU share it and race; it keeps the
+ * previous call's contents (the solver writes all it reads).  The first call on
+ * a device looks up the array's address on that device; make it before any
+ * stream capture.  Errors are returned as statuses only (no message). */
+chase_status chase_heevj_noalloc(const void* G_dev, int64_t ldg, int k, chase_dtype dtype, double* w_host,
+                                 void* Z_dev, int64_t ldz, void* stream);
+
 /* Dense product C = A B (n x n times n x ncols) with the filter's product
  * arithmetic for the given mode; used to check the split-product kernels. */
 chase_status chase_hemm(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, const void* B_dev,

@@ -21,7 +21,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_NOCONV", 4: "ERR_QR_BREAK
 # every symbol include/chase_gb300.h declares
 EXPORTED = ["chase_default_opts", "chase_create", "chase_destroy", "chase_last_error", "chase_workspace_bytes",
             "chase_solve", "chase_solve_batched", "chase_eigvals", "chase_eigvecs", "chase_stats", "chase_backward",
-            "chase_kernel_launch_count", "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_heevj", "chase_hemm",
+            "chase_kernel_launch_count", "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_heevj", "chase_heevj_noalloc", "chase_hemm",
             "chase_generate"]
 
 
@@ -80,6 +80,7 @@ def load() -> C.CDLL:
         "chase_qr": (I, [P, P, I64, I64, I, I]),
         "chase_rayleigh_ritz": (I, [P, P, I64, I64, P, I64, I, P, P]),
         "chase_heevj": (I, [P, P, I64, I, P, P, I64]),
+        "chase_heevj_noalloc": (I, [P, I64, I, I, P, P, I64, P]),
         "chase_hemm": (I, [P, P, I64, I64, P, I64, I, P, I64, I]),
         "chase_generate": (I, [P, P, I64, I64, P, P, P, P, I]),
     }
