@@ -197,6 +197,48 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def backward_timing(pkg, np, torch, dev, n=16384, nev=64, nex=32):
+    """Forward solve + chase_backward on the real symmetric differentiation workload.
+
+    A = Q diag(lam) Q^T (8 reflectors, U[-1,1] with gaps >= 1e-3 among the lowest 80) is generated on the
+    device; the loss sum w_i lambda_i + ||V^T B V||_F^2 uses a seeded symmetric Gaussian B drawn on the device.
+    """
+    from gen import problems as G
+    g = G.rng(5, 1, 0)
+    lam = G.spectrum_gapped(g, n)
+    U = G.gaussian(G.rng(5, 1, 1), (n, 8), False)
+    V0 = G.gaussian(G.rng(5, 1, 2), (n, nev + nex), False)
+    L0 = G.gaussian(G.rng(5, 1, 3), (n, 4), False)
+    w = G.rng(5, 1, 6).standard_normal(nev)
+    Bw, Dw = G.wy_factors(lam, U)
+    tdev = lambda x: torch.from_numpy(np.ascontiguousarray(np.asarray(x).T)).to(dev)
+    s = pkg.Chase(n, nev + nex, complex_=False)
+    At = torch.empty((n, n), dtype=torch.float64, device=dev)
+    s.generate(At, torch.from_numpy(lam).to(dev), tdev(U), tdev(Bw), tdev(Dw))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2205024910 + 5001)
+    Bm = torch.randn((n, n), dtype=torch.float64, device=dev, generator=gen)
+    Bm = 0.5 * (Bm + Bm.T)
+    At.requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam_t, V = pkg.ChaseEigh.apply(At, s, nev, nex, 1e-10, 20, "fp64", tdev(V0), tdev(L0), 1e-10, 20000)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    M = V.T @ Bm @ V
+    loss = (torch.from_numpy(w).to(dev) * lam_t).sum() + (M * M).sum()
+    torch.cuda.synchronize()
+    loss.backward()
+    torch.cuda.synchronize()
+    st = s.stats()
+    out = {"n": n, "nev": nev, "nex": nex, "forward_s": t_fwd, "bwd_ms": st["ms_backward"],
+           "minres_iterations": st["minres_iterations"], "minres_tol": 1e-10,
+           "note": "bwd_ms = chase_backward (in-subspace term, projected MINRES on all 64 columns, Abar, symmetrise)"}
+    s.close()
+    del At, Bm
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -352,6 +394,14 @@ def run_ours(args):
                                                                   "ms_resid")}}
         full.close()
 
+    # backward (adjoint) time on the real symmetric n = 16384 configuration (nev 64, nex 32)
+    bwd = None
+    if not args.no_tts:
+        try:
+            bwd = backward_timing(pkg, np, torch, dev)
+        except Exception as ex:
+            bwd = {"error": repr(ex)[:300]}
+
     cpu = None
     if rank == 0 and ws == 1:
         try:
@@ -369,7 +419,7 @@ def run_ours(args):
                 "data": "synthetic (seeded prescribed-spectrum matrices)",
                 "config": workload_config(args, {"parallelism": "replicas" if ws > 1 else "single GPU"}),
                 "clocks": clk, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "time_to_solution": tts,
+                "time_to_solution": tts, "backward": bwd,
                 "per_step": [{k: round(s[k], 2) if isinstance(s[k], float) else s[k]
                               for k in ("matvecs", "ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_resid",
                                         "ms_filter_kernel", "filter_kernel_launches")} for s in stats]}

@@ -273,12 +273,16 @@ def perturbation_c4(pid: int, step: int, n: int, complex_: bool = True):
 
 
 def spectrum_gapped(g, n: int, nlow: int = 80, gap: float = 1e-3, lo=-1.0, hi=1.0) -> np.ndarray:
-    """Sorted U[lo,hi] spectrum, rejection-resampled until the lowest nlow+1 values have gaps >= gap."""
-    for _ in range(10000):
-        lam = np.sort(g.uniform(lo, hi, size=n))
-        if np.min(np.diff(lam[: nlow + 1])) >= gap:
-            return lam
-    raise RuntimeError("could not draw a gapped spectrum")
+    """U[lo,hi] spectrum whose lowest nlow+1 values have gaps >= gap.
+
+    A sorted uniform sample x is spread as x_i + min(i, nlow+1) g' (g' = gap (hi-lo)/((hi-lo) - (nlow+1) gap))
+    and mapped affinely back onto [lo, hi]: the lowest nlow+1 gaps become >= gap, everything stays sorted.
+    """
+    x = np.sort(g.uniform(lo, hi, size=n))
+    span = hi - lo
+    gp = gap * span / (span - (nlow + 1) * gap)
+    y = x + np.minimum(np.arange(n), nlow + 1) * gp
+    return lo + (y - lo) * span / (span + (nlow + 1) * gp)
 
 
 def problem_c5(n: int = 4096, nev: int = 64, nex: int = 32) -> Problem:

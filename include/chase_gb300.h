@@ -85,6 +85,8 @@ typedef struct {
   double ms_filter_kernel;      /* CUDA-event time of the FP64 split-product filter kernels alone */
   int filter_kernel_launches;   /* launches timed in ms_filter_kernel */
   double ms_filter_kernel_lowp; /* same for the mixed-precision bulk filter kernels */
+  double ms_backward;           /* time of the last chase_backward */
+  int minres_iterations;        /* MINRES iterations of the last chase_backward */
 } chase_stats_t;
 
 /* Kernel launches made by this library in this process so far (all contexts). */

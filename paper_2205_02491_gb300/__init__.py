@@ -3,5 +3,5 @@
 The compute path is the shared library libchase_gb300.so (C ABI in
 include/chase_gb300.h); this package only marshals arguments to it.
 """
-from .api import Chase, colmajor, kernel_launch_count, workspace_bytes  # noqa: F401
+from .api import Chase, ChaseEigh, colmajor, kernel_launch_count, workspace_bytes  # noqa: F401
 from ._lib import MODES, ChaseError, load  # noqa: F401

@@ -38,7 +38,8 @@ class Stats(C.Structure):
                 ("b_sup", C.c_double), ("mu_1", C.c_double), ("mu_ne", C.c_double), ("norm_est", C.c_double),
                 ("max_resid", C.c_double), ("qr_fallbacks", C.c_int), ("filter_launches", C.c_int),
                 ("ms_filter_kernel", C.c_double), ("filter_kernel_launches", C.c_int),
-                ("ms_filter_kernel_lowp", C.c_double)]
+                ("ms_filter_kernel_lowp", C.c_double), ("ms_backward", C.c_double),
+                ("minres_iterations", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -167,6 +167,33 @@ class Chase:
         return At
 
 
+class ChaseEigh(torch.autograd.Function):
+    """Lowest nev eigenpairs of a real symmetric A with a hand-written adjoint (chase_backward).
+
+    forward(A, solver, nev, nex, tol, deg, mode, V0t, L0t, minres_tol, minres_maxit) -> (lam, V), V: n x nev.
+    A is a float64 CUDA tensor (symmetric, so its row-major storage is its column-major storage).
+    The backward uses the solver's last result: run backward before the next solve on the same solver.
+    Gradient: Abar = V (diag(gbar_lam) + F o (V^T Vbar)) V^T + X V^T, X from projected MINRES.
+    """
+
+    @staticmethod
+    def forward(ctx, A, solver, nev, nex, tol, deg, mode, V0t, L0t, minres_tol=1e-12, minres_maxit=5000):
+        At = A.detach().contiguous()
+        w, Vt = solver.solve(At, nev, nex, tol, deg, mode, V0t, L0t)
+        ctx.solver = solver
+        ctx.minres = (minres_tol, minres_maxit)
+        ctx.save_for_backward(At)
+        return w, Vt.mT
+
+    @staticmethod
+    def backward(ctx, gw, gV):
+        (At,) = ctx.saved_tensors
+        gw = gw.contiguous() if gw is not None else None
+        gVt = colmajor(gV) if gV is not None else None
+        gA = ctx.solver.backward(At, gw, gVt, *ctx.minres)
+        return (gA,) + (None,) * 10
+
+
 def kernel_launch_count() -> int:
     """Kernel launches made by the library in this process so far."""
     return int(L.load().chase_kernel_launch_count())

@@ -56,6 +56,10 @@ struct chase_ctx {
   double* lam_locked = nullptr;
   double* bounds = nullptr;
   double* eigvals = nullptr;
+  double* lam_sorted = nullptr;  // all locked eigenvalues of the last solve, ascending
+  int l_final = 0;               // locked pairs of the last solve
+  double* bwd = nullptr;         // adjoint work: 9 blocks n x nev (allocated on first backward)
+  size_t bwd_bytes = 0;
   int* deg = nullptr;
   int* perm = nullptr;
   int* info = nullptr;
@@ -146,13 +150,14 @@ __global__ void nan_check_kernel(int64_t n, int k, const double* X, int64_t ldx,
 }
 
 // rank-sort the l locked eigenvalues, output first nev ascending and the permutation
-__global__ void final_sort_kernel(int l, int nev, const double* lam, double* out, int* perm) {
+__global__ void final_sort_kernel(int l, int nev, const double* lam, double* out, double* all, int* perm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= l) return;
   double wi = lam[i];
   int rank = 0;
   for (int j = 0; j < l; ++j) rank += (lam[j] < wi) || (lam[j] == wi && j < i);
   perm[rank] = i;
+  all[rank] = wi;
   if (rank < nev) out[rank] = wi;
 }
 
@@ -395,6 +400,104 @@ template <typename T> struct Solver {
     copy_cols<T>(st(), n, k, Tv, n, Q, n);
   }
 
+  // ------------------------------------------------------------ adjoint (real symmetric)
+  // Abar = V_S (diag(gl) + F o (V_S^T Vbar)) V_nev^T + X V_nev^T, symmetrised (see adjoint.cu).
+  void backward(const T* A, int64_t lda, const double* gl, const T* gV, int64_t ldg, T* gA, int64_t ldga, double tol,
+                int maxit) {
+    const int64_t n = c->n;
+    const int nev = c->nev, l = c->l_final;
+    CHASE_REQUIRE(l >= nev && nev >= 1, CHASE_ERR_STATE, "no converged pairs to differentiate");
+    CHASE_REQUIRE(gA && ldga >= n && lda >= n && (gV == nullptr || ldg >= n), CHASE_ERR_ARG, "bad backward arguments");
+    CHASE_REQUIRE(tol > 0.0 && maxit >= 1, CHASE_ERR_ARG, "bad MINRES tolerance or iteration cap");
+    const size_t need = 9 * (size_t)n * nev * sizeof(T) + minres_state_bytes(nev) + 256;
+    if (c->bwd_bytes < need) {
+      if (c->bwd) CHASE_CUDA(cudaFree(c->bwd));
+      c->bwd = nullptr;
+      c->bwd_bytes = 0;
+      CHASE_CUDA(cudaMalloc(&c->bwd, need));
+      c->bwd_bytes = need;
+    }
+    T* base = (T*)c->bwd;
+    const int64_t blk = n * nev;
+    T *Tb = base, *Bb = base + blk, *Vv = base + 2 * blk, *Yb = base + 3 * blk, *R1 = base + 4 * blk,
+      *R2 = base + 5 * blk, *Wa = base + 6 * blk, *Wb = base + 7 * blk, *X = base + 8 * blk;
+    void* state = (void*)(base + 9 * blk);
+    const T* Vs = T1();              // locked eigenvectors, ascending (n x l, ld n)
+    const double* lam = c->lam_sorted;
+    T* M = Gb();                     // V_S^T Vbar (l x nev)
+    T* inner = Zb();                 // l x nev
+    oz::invalidate(c->ozw);
+    if (gV) {
+      Epi e;
+      e.C = M;
+      e.ldc = l;
+      gemm(OP_C, Vs, n, OP_N, gV, ldg, l, nev, n, e, CHASE_FP64);
+    }
+    adj_inner(st(), l, nev, lam, gV ? (const double*)M : nullptr, l, gl, (double*)inner, l);
+    Epi et;
+    et.C = Tb;
+    et.ldc = n;
+    gemm(OP_N, Vs, n, OP_N, inner, l, n, nev, l, et, CHASE_FP64);  // T = V_S inner
+    if (gV) {
+      // right-hand sides -P vbar = V_S M - Vbar
+      Epi eb;
+      eb.C = Bb;
+      eb.ldc = n;
+      eb.Y = gV;
+      eb.ldy = ldg;
+      eb.gamma = -1.0;
+      gemm(OP_N, Vs, n, OP_N, M, l, n, nev, l, eb, CHASE_FP64);
+      minres_init(st(), n, nev, (const double*)Bb, n, (double*)R1, (double*)R2, (double*)Vv, (double*)X,
+                  (double*)Wa, (double*)Wb, state, tol);
+      T* Mp = Gb();
+      T *r1 = R1, *r2 = R2, *wc = Wa, *wn = Wb;  // wc: w_{t-1}, wn: w_{t-2}
+      int it = 0;
+      for (; it < maxit; ++it) {
+        Epi ea;
+        ea.C = Yb;
+        ea.ldc = n;
+        ea.Y = Vv;
+        ea.ldy = n;
+        ea.gamma = -1.0;
+        ea.ycol = lam;
+        hemm(A, n, lda, Vv, n, nev, ea, CHASE_FP64);  // Y = A v - lambda_j v
+        Epi ep;
+        ep.C = Mp;
+        ep.ldc = l;
+        gemm(OP_C, Vs, n, OP_N, Yb, n, l, nev, n, ep, CHASE_FP64);
+        Epi eu;
+        eu.C = Yb;
+        eu.ldc = n;
+        eu.alpha = -1.0;
+        eu.Z = Yb;
+        eu.ldz = n;
+        eu.beta = 1.0;
+        gemm(OP_N, Vs, n, OP_N, Mp, l, n, nev, l, eu, CHASE_FP64);  // Y -= V_S (V_S^T Y)
+        minres_update(st(), n, nev, (const double*)Yb, (double*)r1, (const double*)r2, (double*)Vv, (double*)wn,
+                      (const double*)wc, (double*)X, state, tol);
+        std::swap(r1, r2);
+        std::swap(wc, wn);
+        if (it % 10 == 9) {
+          minres_count_done(st(), nev, state, c->status_dev);
+          int done = 0;
+          CHASE_CUDA(cudaMemcpyAsync(&done, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st()));
+          CHASE_CUDA(cudaStreamSynchronize(st()));
+          if (done == nev) break;
+        }
+      }
+      c->stats.minres_iterations = it + 1;
+      add_inplace(st(), blk, (double*)Tb, (const double*)X);
+    }
+    // Abar = (T + X) V_nev^T, then (Abar + Abar^T)/2
+    Epi ga;
+    ga.C = gA;
+    ga.ldc = ldga;
+    gemm_f64<T>(st(), OP_N, OP_C, n, n, nev, Tb, n, Vs, n, ga, W(), c->work_elems);
+    hermitianize<T>(st(), (int)n, gA, ldga);
+    CHASE_CUDA(cudaStreamSynchronize(st()));
+    CHASE_REQUIRE(oz::read_flags(st(), c->ozw) == 0, CHASE_ERR_TIMEOUT, "a tensor-core product hit its wait limit");
+  }
+
   // ------------------------------------------------------------ Algorithm 1
   void solve(const T* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg, int mode, const T* V0,
              const T* L0) {
@@ -543,7 +646,7 @@ template <typename T> struct Solver {
     S.locked = l;
     CHASE_REQUIRE(l >= nev, CHASE_ERR_NOCONV, "maxiter reached before nev pairs converged");
     // final order: nev smallest locked values ascending
-    final_sort_kernel<<<ceil_div(l, 128), 128, 0, st()>>>(l, nev, c->lam_locked, c->eigvals, c->perm);
+    final_sort_kernel<<<ceil_div(l, 128), 128, 0, st()>>>(l, nev, c->lam_locked, c->eigvals, c->lam_sorted, c->perm);
     CHASE_CHECK_LAUNCH();
     // T1 = [locked pairs ascending | remaining active block]: the first nev columns are the
     // eigenvectors, the whole block is a warm start for a nearby problem
@@ -552,6 +655,7 @@ template <typename T> struct Solver {
     c->n = n;
     c->nev = nev;
     c->nex = nex;
+    c->l_final = l;
     c->have_result = true;
     ttot.stop();
   }
@@ -703,6 +807,7 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
     CHASE_CUDA(cudaMalloc(&c->res2, ne_max * sizeof(double)));
     CHASE_CUDA(cudaMalloc(&c->lam_locked, ne_max * sizeof(double)));
     CHASE_CUDA(cudaMalloc(&c->eigvals, ne_max * sizeof(double)));
+    CHASE_CUDA(cudaMalloc(&c->lam_sorted, ne_max * sizeof(double)));
     CHASE_CUDA(cudaMalloc(&c->bounds, 8 * sizeof(double)));
     CHASE_CUDA(cudaMalloc(&c->deg, ne_max * sizeof(int)));
     CHASE_CUDA(cudaMalloc(&c->perm, ne_max * sizeof(int)));
@@ -722,7 +827,8 @@ void chase_destroy(chase_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
-                  c->lam_locked, c->eigvals, c->bounds, c->deg, c->perm, c->info, c->status_dev};
+                  c->lam_locked, c->eigvals, c->lam_sorted, c->bwd, c->bounds, c->deg, c->perm, c->info,
+                  c->status_dev};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   oz::destroy(c->ozw);
@@ -910,8 +1016,11 @@ chase_status chase_backward(chase_ctx* c, const void* A, int64_t lda, const doub
   API_BEGIN(c)
   CHASE_REQUIRE(c->dtype == CHASE_R64, CHASE_ERR_UNSUPPORTED, "backward implemented for real symmetric problems");
   CHASE_REQUIRE(c->have_result, CHASE_ERR_STATE, "no solve result");
-  (void)A; (void)lda; (void)gl; (void)gV; (void)ldg; (void)gA; (void)ldga; (void)minres_tol; (void)minres_maxit;
-  CHASE_REQUIRE(false, CHASE_ERR_UNSUPPORTED, "backward not built yet");
+  CHASE_REQUIRE(A != nullptr, CHASE_ERR_ARG, "null A");
+  Timer t(c, 0, &c->stats.ms_backward);
+  Solver<double>(c).backward((const double*)A, lda, gl, (const double*)gV, ldg, (double*)gA, ldga, minres_tol,
+                             minres_maxit);
+  t.stop();
   API_END(c)
 }
 

@@ -68,4 +68,15 @@ void bookkeeping(cudaStream_t st, int k, const double* ritz, const double* res, 
                  double* bounds, int maxdeg, int extra_deg, int* out_lock, int* out_deg, int* out_perm,
                  double* out_ritz, double* out_res, int* scratch);
 
+// adjoint helpers (adjoint.cu)
+void adj_inner(cudaStream_t st, int l, int nev, const double* lam, const double* M, int64_t ldm, const double* gl,
+               double* inner, int64_t ldi);
+void minres_init(cudaStream_t st, int64_t n, int nev, const double* B, int64_t ldb, double* R1, double* R2,
+                 double* Vv, double* X, double* W, double* W2, void* state, double tol);
+void minres_update(cudaStream_t st, int64_t n, int nev, const double* Y, double* R1, const double* R2, double* Vv,
+                   double* Wn, const double* Wc, double* X, void* state, double tol);
+void minres_count_done(cudaStream_t st, int nev, const void* state, int* out);
+void add_inplace(cudaStream_t st, int64_t count, double* a, const double* b);
+size_t minres_state_bytes(int nev);
+
 }  // namespace chase

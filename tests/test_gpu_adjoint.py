@@ -1,0 +1,111 @@
+"""GPU adjoint (chase_backward through ChaseEigh) against the dense reference gradient and
+central finite differences of the exact loss L(A) = sum w_i lambda_i + ||V^T B V||_F^2."""
+import numpy as np
+import pytest
+
+from gen import problems as G
+from oracle import chase_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2205_02491_gb300 as P
+    return P
+
+
+def _problem(n, nev, nex, gap, seed):
+    g = np.random.default_rng(seed)
+    low = -1.0 + gap * np.arange(nev + 2)
+    rest = np.sort(g.uniform(low[-1] + gap, 1.0, n - nev - 2))
+    lam = np.concatenate([low, rest])
+    p = G.problem_small(n, nev, nex, complex_=False, k_reflect=6, lam=lam, seed_pid=seed, cfg=10)
+    w = g.standard_normal(nev)
+    Bm = g.standard_normal((n, n))
+    return p, w, 0.5 * (Bm + Bm.T)
+
+
+def _exact_loss(A, nev, w, Bm):
+    lam, V = np.linalg.eigh(A)
+    M = V[:, :nev].T @ Bm @ V[:, :nev]
+    return float(w @ lam[:nev] + np.sum(M * M))
+
+
+def _gpu_grad(pkg, p, A, w, Bm, tol=1e-13, minres_tol=1e-13):
+    import torch
+    s = pkg.Chase(p.n, p.ne, complex_=False)
+    At = torch.from_numpy(A.copy()).cuda().requires_grad_(True)
+    V0t = torch.from_numpy(np.ascontiguousarray(p.V0.T)).cuda()
+    L0t = torch.from_numpy(np.ascontiguousarray(p.L0.T)).cuda()
+    lam, V = pkg.ChaseEigh.apply(At, s, p.nev, p.nex, tol, p.deg, "fp64", V0t, L0t, minres_tol, 20000)
+    Bt = torch.from_numpy(Bm).cuda()
+    M = V.T @ Bt @ V
+    L = (torch.from_numpy(w).cuda() * lam).sum() + (M * M).sum()
+    L.backward()
+    st = s.stats()
+    return float(L.item()), At.grad.cpu().numpy(), st
+
+
+def test_backward_matches_dense_reference(pkg):
+    p, w, Bm = _problem(400, 12, 8, 0.02, 3)
+    A = p.dense()
+    L, gA, st = _gpu_grad(pkg, p, A, w, Bm)
+    lam, V = np.linalg.eigh(A)
+    V = V[:, :12]
+    gV = 4.0 * Bm @ V @ (V.T @ Bm @ V)
+    ref = O.eig_backward_dense(A, w, gV, 12)
+    assert np.max(np.abs(gA - ref)) <= 1e-8 * np.max(np.abs(ref))
+    assert np.max(np.abs(gA - gA.T)) == 0.0
+    assert st["minres_iterations"] >= 1
+
+
+def test_backward_central_differences(pkg):
+    n, nev = 300, 8
+    p, w, Bm = _problem(n, nev, 6, 0.05, 5)
+    A = p.dense()
+    L, gA, _ = _gpu_grad(pkg, p, A, w, Bm)
+    assert abs(L - _exact_loss(A, nev, w, Bm)) <= 1e-9 * abs(L)
+    g = np.random.default_rng(9)
+    h = 1e-5
+    for _ in range(3):
+        D = g.standard_normal((n, n))
+        D = 0.5 * (D + D.T)
+        fd = (_exact_loss(A + h * D, nev, w, Bm) - _exact_loss(A - h * D, nev, w, Bm)) / (2 * h)
+        an = float(np.sum(gA * D))
+        assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+def test_backward_eigenvalue_only(pkg):
+    import torch
+    p, w, _ = _problem(200, 6, 6, 0.05, 7)
+    A = p.dense()
+    s = pkg.Chase(p.n, p.ne, complex_=False)
+    At = torch.from_numpy(A.copy()).cuda().requires_grad_(True)
+    V0t = torch.from_numpy(np.ascontiguousarray(p.V0.T)).cuda()
+    L0t = torch.from_numpy(np.ascontiguousarray(p.L0.T)).cuda()
+    lam, V = pkg.ChaseEigh.apply(At, s, p.nev, p.nex, 1e-12, p.deg, "fp64", V0t, L0t)
+    (torch.from_numpy(w).cuda() * lam).sum().backward()
+    Vh = V.detach().cpu().numpy()
+    assert np.max(np.abs(At.grad.cpu().numpy() - Vh @ np.diag(w) @ Vh.T)) <= 1e-13
+
+
+def test_backward_c5_gradient_check(pkg):
+    # the n = 4096 real symmetric configuration (nev 64, nex 32, gapped lowest 80): dense reference gradient
+    p = G.problem_c5(4096)
+    A = p.dense()
+    w, Bm = p.extra["w"], p.extra["B"]
+    L, gA, st = _gpu_grad(pkg, p, A, w, Bm, tol=1e-12, minres_tol=1e-11)
+    lam, Vall = np.linalg.eigh(A)
+    V = Vall[:, :64]
+    assert np.min(np.diff(lam[:81])) >= 1e-3 * (1 - 1e-12)
+    gV = 4.0 * Bm @ V @ (V.T @ Bm @ V)
+    gl = np.zeros(A.shape[0])
+    gl[:64] = w
+    Vb = np.zeros_like(Vall)
+    Vb[:, :64] = gV
+    ref = O._dense_grad(lam, Vall, gl, Vb)
+    assert np.max(np.abs(gA - ref)) <= 1e-6 * np.max(np.abs(ref))
