@@ -254,22 +254,54 @@ def problem_c4(pid: int, n: int | None = None) -> Problem:
     return _make(f"c4.{pid}", 4, pid + 1, n, nev, nex, lam, 8, True)
 
 
-def perturbation_c4(pid: int, step: int, n: int, complex_: bool = True):
-    """Seeded Hermitian Gaussian H = (G + G^H)/2 as a low-cost generator description.
+_M64 = (1 << 64) - 1
 
-    Returns (G, scale): H = scale * (G + G^H)/2 with scale = 1/||(G+G^H)/2||_2 estimated
-    by 60 power iterations on the host (adequate to 1e-6 relative for the 1e-3 step size).
+
+def _splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) on uint64 arrays (wrapping arithmetic)."""
+    with np.errstate(over="ignore"):
+        z = (x + np.uint64(0x9E3779B97F4A7C15)).astype(np.uint64)
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)).astype(np.uint64)
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)).astype(np.uint64)
+        return z ^ (z >> np.uint64(31))
+
+
+def counter_normal_pairs(seed: int, ctr: np.ndarray):
+    """Counter-based standard normal pairs: SplitMix64 hash of (seed, 2c) and (seed, 2c+1), Box-Muller."""
+    s = np.uint64(seed & _M64)
+    c = ctr.astype(np.uint64)
+    a = _splitmix64(s ^ _splitmix64(np.uint64(2) * c))
+    b = _splitmix64(s ^ _splitmix64(np.uint64(2) * c + np.uint64(1)))
+    u1 = ((a >> np.uint64(11)).astype(np.float64) + 1.0) * 1.1102230246251565e-16
+    u2 = (b >> np.uint64(11)).astype(np.float64) * 1.1102230246251565e-16
+    r = np.sqrt(-2.0 * np.log(u1))
+    t = 6.283185307179586 * u2
+    return r * np.cos(t), r * np.sin(t)
+
+
+def perturbation(n: int, seed: int, complex_: bool = True) -> np.ndarray:
+    """H = s (G + G^H)/2 with G_ij from counter_normal_pairs(seed, i + j n), s = 1/sqrt(2n).
+
+    Complex: G_ij = (x + i y)/sqrt(2); real: G_ij = x.  s is the semicircle-edge estimate of
+    1/||(G+G^H)/2||_2 (the spectral normalisation of the correlated-sequence workload).
     """
-    g = rng(4, 1000 + pid * 8 + step, _S_PERTURB)
-    G = gaussian(g, (n, n), complex_)
-    H = 0.5 * (G + np.conj(G.T))
-    x = gaussian(g, (n,), complex_)
-    x /= np.linalg.norm(x)
-    for _ in range(60):
-        y = H @ x
-        nrm = np.linalg.norm(y)
-        x = y / nrm
-    return H / nrm
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    x, y = counter_normal_pairs(seed, (i + j * n).reshape(-1))
+    x = x.reshape(n, n)
+    y = y.reshape(n, n)
+    s = 1.0 / np.sqrt(2.0 * n)
+    if complex_:
+        Gm = (x + 1j * y) * np.sqrt(0.5)
+        H = 0.5 * (Gm + np.conj(Gm.T))
+        H[np.arange(n), np.arange(n)] = np.real(np.diag(H))
+    else:
+        H = 0.5 * (x + x.T)
+    return s * H
+
+
+def sequence_seed(pid: int, step: int) -> int:
+    return (SEED_BASE + 4 * 1000 + pid) * 16 + step
 
 
 def spectrum_gapped(g, n: int, nlow: int = 80, gap: float = 1e-3, lo=-1.0, hi=1.0) -> np.ndarray:

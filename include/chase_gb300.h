@@ -208,6 +208,13 @@ chase_status chase_hemm(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t ld
 chase_status chase_generate(chase_ctx* ctx, void* A_dev, int64_t n, int64_t lda, const double* lam_dev,
                             const void* U_dev, const void* B_dev, const void* D_dev, int k);
 
+/* Input generator for correlated sequences (not part of Algorithm 1): A += eps * H with
+ * H = s (G + G^H)/2, G_ij standard (complex) Gaussian from a counter-based generator
+ * (SplitMix64 hash of the seed and the element's counter, Box-Muller), s = 1/sqrt(2n) the
+ * semicircle-edge estimate of 1/||(G+G^H)/2||_2 (real: G_ij ~ N(0,1), same s).  Keeps A
+ * exactly Hermitian.  The same generator is available on the host for parity checks. */
+chase_status chase_perturb(chase_ctx* ctx, void* A_dev, int64_t n, int64_t lda, double eps, uint64_t seed);
+
 #ifdef __cplusplus
 }
 #endif

@@ -160,6 +160,12 @@ class Chase:
         self._chk(self.lib.chase_hemm(self.ctx, _ptr(At), n, n, _ptr(Bt), n, k, _ptr(Ct), n, mode))
         return Ct
 
+    def perturb(self, At, eps: float, seed: int):
+        """A += eps * H(seed) in place (seeded Hermitian Gaussian of spectral norm about 1)."""
+        n = At.shape[-1]
+        self._chk(self.lib.chase_perturb(self.ctx, _ptr(At), n, n, float(eps), int(seed) & ((1 << 64) - 1)))
+        return At
+
     def generate(self, At, lam, Ut, Bt, Dt):
         n = At.shape[-1]
         k = Ut.shape[0]

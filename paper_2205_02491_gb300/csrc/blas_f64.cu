@@ -489,6 +489,60 @@ void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* la
   CHASE_CHECK_LAUNCH();
 }
 
+// ============================================================== seeded Hermitian perturbation
+// Counter-based Gaussian: SplitMix64 (Steele, Lea & Flood 2014) as a hash of (seed, counter), two 53-bit
+// uniforms per draw, Box-Muller.  G_ij (complex) uses counter 2 (i + j n) and 2 (i + j n) + 1; real uses one
+// normal.  A += eps * s * (G + G^H)/2 with s = 1/sqrt(2n) (complex) or 1/sqrt(2n) * sqrt(2) (real), the
+// semicircle-edge estimate of 1/||(G+G^H)/2||_2.
+__device__ inline unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ inline double2 normal_pair(unsigned long long seed, unsigned long long ctr) {
+  unsigned long long a = splitmix64(seed ^ splitmix64(2 * ctr));
+  unsigned long long b = splitmix64(seed ^ splitmix64(2 * ctr + 1));
+  double u1 = ((double)(a >> 11) + 1.0) * 1.1102230246251565e-16;  // (0, 1]
+  double u2 = (double)(b >> 11) * 1.1102230246251565e-16;           // [0, 1)
+  double r = sqrt(-2.0 * log(u1));
+  double t = 6.283185307179586 * u2;
+  return make_double2(r * cos(t), r * sin(t));
+}
+
+template <typename T>
+__global__ void perturb_kernel(T* A, int64_t n, int64_t lda, double eps, unsigned long long seed) {
+  using s = S<T>;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t j = blockIdx.y;
+  if (i >= n || i < j) return;
+  const double sc = s::cplx ? eps / sqrt(2.0 * (double)n) : eps / sqrt(2.0 * (double)n);
+  double2 gij = normal_pair(seed, (unsigned long long)(i + j * n));
+  double2 gji = normal_pair(seed, (unsigned long long)(j + i * n));
+  if (s::cplx) {
+    // G = (x + i y)/sqrt(2): h_ij = (G_ij + conj(G_ji))/2
+    double hr = 0.5 * 0.7071067811865476 * (gij.x + gji.x);
+    double hi = 0.5 * 0.7071067811865476 * (gij.y - gji.y);
+    if (i == j) hi = 0.0;
+    T d = s::make(sc * hr, sc * hi);
+    A[i + j * lda] = s::add(A[i + j * lda], d);
+    if (i != j) A[j + i * lda] = s::add(A[j + i * lda], s::conj(d));
+  } else {
+    double h = 0.5 * (gij.x + gji.x);
+    T d = s::make(sc * h, 0.0);
+    A[i + j * lda] = s::add(A[i + j * lda], d);
+    if (i != j) A[j + i * lda] = s::add(A[j + i * lda], d);
+  }
+}
+
+template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda, double eps, unsigned long long seed) {
+  CHASE_REQUIRE(n <= 65535, 1, "perturbation supports n <= 65535");
+  dim3 grid(ceil_div(n, 256), (unsigned)n);
+  perturb_kernel<T><<<grid, 256, 0, st>>>(A, n, lda, eps, seed);
+  CHASE_CHECK_LAUNCH();
+}
+
 // ============================================================== instantiations
 #define INST(T)                                                                                                   \
   template void gemm_f64<T>(cudaStream_t, Op, Op, int64_t, int64_t, int64_t, const T*, int64_t, const T*, int64_t, \
@@ -505,7 +559,8 @@ void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* la
   template void trsm_right_lh<T>(cudaStream_t, int64_t, int, T*, int64_t, const T*, int64_t, T*, int64_t);        \
   template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int); \
   template void zero_upper<T>(cudaStream_t, int, T*, int64_t);                                                    \
-  template void trtri_diag<T>(cudaStream_t, int, T*, int64_t);
+  template void trtri_diag<T>(cudaStream_t, int, T*, int64_t);                                                   \
+  template void perturb<T>(cudaStream_t, T*, int64_t, int64_t, double, unsigned long long);
 INST(double)
 INST(double2)
 #undef INST

@@ -985,6 +985,17 @@ chase_status chase_generate(chase_ctx* c, void* A, int64_t n, int64_t lda, const
   API_END(c)
 }
 
+chase_status chase_perturb(chase_ctx* c, void* A, int64_t n, int64_t lda, double eps, uint64_t seed) {
+  API_BEGIN(c)
+  CHASE_REQUIRE(A && n >= 1 && lda >= n, CHASE_ERR_ARG, "bad args");
+  if (c->dtype == CHASE_C128)
+    perturb<double2>(c->stream, (double2*)A, n, lda, eps, (unsigned long long)seed);
+  else
+    perturb<double>(c->stream, (double*)A, n, lda, eps, (unsigned long long)seed);
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  API_END(c)
+}
+
 chase_status chase_solve_batched(chase_ctx* c, int nprob, const void* const* A, const int64_t* n, const int* nev,
                                  const int* nex, double tol, int deg, int mode, void* const* Vd, const void* const* L0,
                                  double* const* eigvals, chase_stats_t* stats_host) {

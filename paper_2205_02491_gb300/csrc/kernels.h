@@ -63,6 +63,10 @@ template <typename T>
 void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* lam, const T* U, const T* B,
                  const T* D, int k);
 
+// A += eps * H(seed), H a counter-based seeded Hermitian Gaussian scaled to spectral norm about 1.
+template <typename T>
+void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda, double eps, unsigned long long seed);
+
 // Bookkeeping (Algorithm 1, lines 8-14) on the device.  See chase.cu for the layout of `bk`.
 void bookkeeping(cudaStream_t st, int k, const double* ritz, const double* res, double thresh, double b_sup,
                  double* bounds, int maxdeg, int extra_deg, int* out_lock, int* out_deg, int* out_perm,

@@ -1,0 +1,60 @@
+"""Batched solves of correlated sequences A_{k+1} = A_k + 1e-3 H_k with warm starts (GPU)."""
+import numpy as np
+import pytest
+
+from gen import problems as G
+from tests.helpers import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2205_02491_gb300 as P
+    return P
+
+
+def test_device_perturbation_matches_host(pkg):
+    for cplx in (True, False):
+        n = 257
+        A = G.problem_small(n, 2, 2, complex_=cplx).dense()
+        s = pkg.Chase(n, 4, complex_=cplx)
+        At = dev(A)
+        s.perturb(At, 1e-3, 99)
+        ref = A + 1e-3 * G.perturbation(n, 99, cplx)
+        got = host(At)
+        assert np.max(np.abs(got - ref)) <= 1e-15
+        assert np.array_equal(got, np.conj(got.T))
+
+
+def test_batched_warm_start_sequence(pkg):
+    ns = [300, 420, 515]
+    probs = [G.problem_c4(pid, n) for pid, n in enumerate(ns)]
+    nevs = [p.nev for p in probs]
+    nexs = [p.nex for p in probs]
+    ctx = pkg.Chase(max(ns), max(p.ne for p in probs), complex_=True)
+    A_host = [p.dense() for p in probs]
+    A_dev = [dev(a) for a in A_host]
+    V = [dev(p.V0) for p in probs]
+    L0 = [dev(p.L0) for p in probs]
+    mv = []
+    for step in range(3):
+        ws, stats = ctx.solve_batched(A_dev, nevs, nexs, 1e-10, 20, "fp64", V, L0)
+        mv.append([st["matvecs"] for st in stats])
+        for q, p in enumerate(probs):
+            ref = np.linalg.eigvalsh(A_host[q])[: p.nev]
+            nrm = np.max(np.abs(np.linalg.eigvalsh(A_host[q])))
+            w = ws[q].cpu().numpy()
+            assert np.max(np.abs(w - ref)) <= 1e-10 * nrm
+            Vq = host(V[q])[:, : p.nev]
+            R = A_host[q] @ Vq - Vq * w[None, :]
+            assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
+            seed = G.sequence_seed(q, step)
+            ctx.perturb(A_dev[q], 1e-3, seed)
+            A_host[q] = A_host[q] + 1e-3 * G.perturbation(p.n, seed, True)
+    # warm starts from the previous eigenvectors need fewer filter products than the cold start
+    for q in range(len(probs)):
+        assert max(mv[1][q], mv[2][q]) < mv[0][q]
