@@ -166,6 +166,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -317,28 +325,34 @@ __global__ void __maxnreg__(168)
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     constexpr uint32_t IDESC = idesc_bf16(BM, Cf::NT);
-    bool first[Cf::NACC];
-#pragma unroll
-    for (int a = 0; a < Cf::NACC; ++a) first[a] = true;
+    // bit a set: the next MMA into accumulator a starts it (enable_input_d = 0)
+    uint32_t fresh = (1u << Cf::NACC) - 1u;
     int a_iter = 0;
     bool ok = true;
-    // all MMAs of pair (t, u) over this k-block's two K-steps into accumulator acc
-    auto issue_pair = [&](uint32_t abase, uint32_t bbase, int t, int u) {
-      const int level = t + u;
-      const int acc = level < NEX ? level : NEX;
-      const uint32_t dt = tmem + (uint32_t)(acc * Cf::NT);
+    // MMAs of slice t (all its pairs in `pass`: 0 all, 1 inexact levels, 2 exact levels), both K-steps.
+    // t and u are compile-time after unrolling, so level, accumulator and descriptor offsets fold.
+    auto issue_slice = [&](const int t, const int pass, const uint64_t adesc, const uint64_t bdesc) {
 #pragma unroll
-      for (int ks = 0; ks < BK / 16; ++ks) {
-        const uint32_t koff = ks * 32;
-        if (CPLX) {
-          const uint32_t b_slice = bbase + u * Cf::B_SLICE;
-          // [Cr | Ci] += Ar [Yr | Yi] + Ai [-Yi | Yr]
-          mma_bf16(dt, sw64_desc(abase + koff), sw64_desc(b_slice + Cf::B_PLANE + koff), IDESC, first[acc] ? 0u : 1u);
-          first[acc] = false;
-          mma_bf16(dt, sw64_desc(abase + Cf::A_PLANE + koff), sw64_desc(b_slice + koff), IDESC, 1u);
-        } else {
-          mma_bf16(dt, sw64_desc(abase + koff), sw64_desc(bbase + u * Cf::B_SLICE + koff), IDESC, first[acc] ? 0u : 1u);
-          first[acc] = false;
+      for (int u = S - 1; u >= 0; --u) {
+        if (u > Cf::MAXLEVEL - t) continue;
+        const int level = t + u;
+        if (pass == 1 && level < NEX) continue;
+        if (pass == 2 && level >= NEX) continue;
+        const int acc = level < NEX ? level : NEX;
+        const uint32_t dt = tmem + (uint32_t)(acc * Cf::NT);
+        const uint64_t bslice = bdesc + (uint64_t)((u * Cf::B_SLICE) >> 4);
+#pragma unroll
+        for (int ks = 0; ks < BK / 16; ++ks) {
+          const uint64_t ko = (uint64_t)(ks * 2);  // 32 bytes along K, in 16-byte units
+          const uint32_t en = ((fresh >> acc) & 1u) ? 0u : 1u;
+          fresh &= ~(1u << acc);
+          if (CPLX) {
+            // [Cr | Ci] += Ar [Yr | Yi] + Ai [-Yi | Yr]
+            mma_bf16(dt, adesc + ko, bslice + (uint64_t)(Cf::B_PLANE >> 4) + ko, IDESC, en);
+            mma_bf16(dt, adesc + (uint64_t)(Cf::A_PLANE >> 4) + ko, bslice + ko, IDESC, 1u);
+          } else {
+            mma_bf16(dt, adesc + ko, bslice + ko, IDESC, en);
+          }
         }
       }
     };
@@ -351,50 +365,43 @@ __global__ void __maxnreg__(168)
         break;
       }
       fence_after();
-      if (chunk_start)
-        for (int a = 0; a < NEX; ++a) first[a] = true;
-      const uint32_t bbase = smem_u32(sB + bs * Cf::B_STAGE);
+      if (chunk_start) fresh |= (1u << NEX) - 1u;  // exact levels restart every chunk
+      const uint64_t bdesc = sw64_desc(smem_u32(sB + bs * Cf::B_STAGE));
       if (!(NEX > 0 && chunk_start && chunk > 0)) {
         // one pass: slices in descending order, pairs of each slice inexact-first
-        for (int ti = 0; ti < S && ok; ++ti, ++a_iter) {
-          const int t = S - 1 - ti;
-          const int as = a_iter % Cf::A_SLOTS;
-          if (!mbar_wait(smem_u32(&a_full[as]), (a_iter / Cf::A_SLOTS) & 1, abort_sh, err)) {
-            ok = false;
-            break;
-          }
+#pragma unroll
+        for (int ti = 0; ti < S; ++ti) {
+          const int as = (a_iter + ti) % Cf::A_SLOTS;
+          if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
+          if (!ok) break;
           fence_after();
-          const uint32_t abase = smem_u32(sA + as * Cf::A_SLOT);
-          for (int u = Cf::MAXLEVEL - t; u >= 0; --u) issue_pair(abase, bbase, t, u);
+          issue_slice(S - 1 - ti, 0, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
           mma_commit(smem_u32(&a_empty[as]));
         }
+        if (!ok) break;
+        a_iter += S;
       } else {
         // first k-block of a chunk: every inexact pair of the k-block runs while the epilogue
         // flushes the exact accumulators of the previous chunk, then the exact pairs
-        for (int ti = 0; ti < S && ok; ++ti) {
-          const int t = S - 1 - ti;
+#pragma unroll
+        for (int ti = 0; ti < S; ++ti) {
           const int as = (a_iter + ti) % Cf::A_SLOTS;
-          if (!mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) {
-            ok = false;
-            break;
-          }
+          if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
+          if (!ok) break;
           fence_after();
-          const uint32_t abase = smem_u32(sA + as * Cf::A_SLOT);
-          for (int u = Cf::MAXLEVEL - t; u >= 0 && t + u >= NEX; --u) issue_pair(abase, bbase, t, u);
+          issue_slice(S - 1 - ti, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
         }
         if (ok && !mbar_wait(smem_u32(tmem_empty), (chunk - 1) & 1, abort_sh, err)) ok = false;
         if (!ok) break;
         fence_after();
-        for (int ti = 0; ti < S; ++ti, ++a_iter) {
-          const int t = S - 1 - ti;
-          const int as = a_iter % Cf::A_SLOTS;
-          const uint32_t abase = smem_u32(sA + as * Cf::A_SLOT);
-          for (int u = (NEX - 1 - t < Cf::MAXLEVEL - t ? NEX - 1 - t : Cf::MAXLEVEL - t); u >= 0; --u)
-            issue_pair(abase, bbase, t, u);
+#pragma unroll
+        for (int ti = 0; ti < S; ++ti) {
+          const int as = (a_iter + ti) % Cf::A_SLOTS;
+          issue_slice(S - 1 - ti, 2, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
           mma_commit(smem_u32(&a_empty[as]));
         }
+        a_iter += S;
       }
-      if (!ok) break;
       mma_commit(smem_u32(&b_empty[bs]));
       // exact levels: one commit per chunk (the epilogue consumes each before the next
       // chunk's exact MMAs start); single-accumulator modes: one commit at the end
@@ -428,23 +435,19 @@ __global__ void __maxnreg__(168)
       fence_after();
       if (NEX > 0) {
 #pragma unroll
-        for (int h = 0; h < EPI_COLS / 8; ++h) {
-          long long part[8];
+        for (int L = 0; L < (NEX > 0 ? NEX : 1); ++L) {
+          // all columns of one level in flight, one wait
+          uint32_t r[EPI_COLS];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) part[j] = 0;
+          for (int h = 0; h < EPI_COLS / 8; ++h)
+            tmem_ld8_nowait(lane_addr + (uint32_t)(L * Cf::NT + wg * EPI_COLS + h * 8), &r[h * 8]);
+          tmem_wait_ld();
+          const float sc = (float)(1ull << (8 * L));  // level L unit is 2^-8L
 #pragma unroll
-          for (int L = 0; L < (NEX > 0 ? NEX : 1); ++L) {
-            uint32_t r[8];
-            tmem_ld8(lane_addr + (uint32_t)(L * Cf::NT + wg * EPI_COLS + h * 8), r);
-            const float sc = (float)(1ull << (8 * L));  // level L unit is 2^-8L
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const long long iv = (long long)__float2int_rn(__uint_as_float(r[j]) * sc);
-              part[j] += iv << (8 * (NEX - 1 - L));
-            }
+          for (int j = 0; j < EPI_COLS; ++j) {
+            const long long iv = (long long)__float2int_rn(__uint_as_float(r[j]) * sc);
+            acc64[j] += iv << (8 * (NEX - 1 - L));
           }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc64[h * 8 + j] += part[j];
         }
         fence_before();
         __syncwarp();
