@@ -87,6 +87,8 @@ typedef struct {
   double ms_filter_kernel_lowp; /* same for the mixed-precision bulk filter kernels */
   double ms_backward;           /* time of the last chase_backward */
   int minres_iterations;        /* MINRES iterations of the last chase_backward */
+  int rr_clusters;              /* eigenvalue clusters solved exactly in the Rayleigh-Ritz eigensolves */
+  int rr_fallbacks;             /* Rayleigh-Ritz eigensolves that fell back to the FP64 Jacobi */
 } chase_stats_t;
 
 /* Kernel launches made by this library in this process so far (all contexts). */

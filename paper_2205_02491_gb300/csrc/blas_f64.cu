@@ -564,5 +564,8 @@ template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda
 INST(double)
 INST(double2)
 #undef INST
+// single-precision first pass of the Rayleigh-Ritz eigensolve
+template void permute_cols<float>(cudaStream_t, int64_t, int, const float*, int64_t, float*, int64_t, const int*);
+template void permute_cols<float2>(cudaStream_t, int64_t, int, const float2*, int64_t, float2*, int64_t, const int*);
 
 }  // namespace chase

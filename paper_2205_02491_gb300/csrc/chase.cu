@@ -367,6 +367,130 @@ template <typename T> struct Solver {
     CHASE_REQUIRE(ok, CHASE_ERR_QR_BREAKDOWN, "Cholesky-QR breakdown after the shifted fallback");
   }
 
+  // ------------------------------------------------------------ Rayleigh-Ritz eigensolve
+  // Z (k x k, orthonormal columns) <- Z L^{-H} with G_z = Z^H Z = L L^H.  Returns false if not SPD.
+  bool orthonormalize_small(T* Z, int k, T* Gm, T* tmp) {
+    Epi e;
+    e.C = Gm;
+    e.ldc = k;
+    gemm(OP_C, Z, k, OP_N, Z, k, k, k, k, e, CHASE_FP64);
+    hermitianize<T>(st(), k, Gm, k);
+    CHASE_CUDA(cudaMemsetAsync(c->info, 0, sizeof(int), st()));
+    potrf_lower<T>(st(), k, Gm, k, c->info, W(), c->work_elems);
+    int info = 0;
+    CHASE_CUDA(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, st()));
+    CHASE_CUDA(cudaStreamSynchronize(st()));
+    if (info != 0) return false;
+    if (use_split(CHASE_FP64, k, k, k)) {
+      zero_upper<T>(st(), k, Gm, k);
+      trtri_diag<T>(st(), k, Gm, k);
+      trtri_combine(Gm, k, k, tmp, CHASE_FP64);
+      Epi q;
+      q.C = Z;
+      q.ldc = k;
+      gemm(OP_N, Z, k, OP_C, Gm, k, k, k, k, q, CHASE_FP64);
+    } else {
+      trsm_right_lh<T>(st(), k, k, Z, k, Gm, k, W(), c->work_elems);
+    }
+    return true;
+  }
+
+  // Eigenpairs of the Hermitian G = Gb() (k x k): FP32 parallel Jacobi, two first-order refinement
+  // steps in FP64-class products, exact FP64 Jacobi on clusters closer than omega.  Ascending
+  // eigenvalues to w (device), eigenvectors to Zb().  scratch: 3 k*k scalars.  Returns false when a
+  // step cannot be completed (the caller then uses the FP64 Jacobi solver).
+  // verbose-mode probe: report non-finite entries of a device block
+  void dbg_finite(const void* X, int64_t rows, int cols, int64_t ld, size_t esz, const char* what) {
+    if (!verbose()) return;
+    CHASE_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), st()));
+    int64_t r = rows * (int64_t)(esz / sizeof(double));
+    dim3 grid(std::min<unsigned>(ceil_div(r, 256), 64), cols);
+    nan_check_kernel<<<grid, 256, 0, st()>>>(r, cols, (const double*)X, ld * (int64_t)(esz / sizeof(double)),
+                                             c->status_dev);
+    CHASE_CHECK_LAUNCH();
+    int flag = 0;
+    CHASE_CUDA(cudaMemcpyAsync(&flag, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st()));
+    CHASE_CUDA(cudaStreamSynchronize(st()));
+    if (flag) fprintf(stderr, "[chase] non-finite values in %s (%lld x %d)\n", what, (long long)rows, cols);
+  }
+
+  bool eigh_mixed(int k, double* w, T* scratch) {
+    using F = typename Lowp<T>::type;
+    T* G = Gb();
+    T* Z = Zb();
+    T *Wk = scratch, *Gp = scratch + (size_t)k * k, *X = scratch + 2 * (size_t)k * k;
+    F* Gf = (F*)W();
+    F* Zf = Gf + (size_t)k * k;
+    F* jw = Zf + (size_t)k * k;
+    const int64_t jw_elems = (c->work_elems * (int64_t)sizeof(T)) / (int64_t)sizeof(F) - 2 * (int64_t)k * k;
+    if (jw_elems < (int64_t)k * k + 3 * (int64_t)k + 8) return false;
+    dbg_finite(G, k, k, k, sizeof(T), "G before the FP32 pass");
+    convert_mat<T, F>(st(), k, G, k, Gf, k);
+    try {
+      heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40, false);
+    } catch (const Error& e) {
+      if (e.status != CHASE_ERR_NAN) throw;
+      return false;  // G itself is untouched: the FP64 solver takes over
+    }
+    convert_mat<F, T>(st(), k, Zf, k, Z, k);
+    dbg_finite(Z, k, k, k, sizeof(T), "Z after the FP32 pass");
+    double ends[2];
+    CHASE_CUDA(cudaMemcpyAsync(&ends[0], w, sizeof(double), cudaMemcpyDeviceToHost, st()));
+    CHASE_CUDA(cudaMemcpyAsync(&ends[1], w + (k - 1), sizeof(double), cudaMemcpyDeviceToHost, st()));
+    CHASE_CUDA(cudaStreamSynchronize(st()));
+    const double scale = std::max(std::fabs(ends[0]), std::fabs(ends[1]));
+    if (!(scale > 0.0) || !std::isfinite(scale)) return false;
+    const double omega = 1e-5 * scale;
+    for (int it = 0; it < 3; ++it) {
+      if (!orthonormalize_small(Z, k, Gp, X)) return false;
+      Epi e1;
+      e1.C = Wk;
+      e1.ldc = k;
+      gemm(OP_N, G, k, OP_N, Z, k, k, k, k, e1, CHASE_FP64);  // G Z
+      Epi e2;
+      e2.C = Gp;
+      e2.ldc = k;
+      gemm(OP_C, Z, k, OP_N, Wk, k, k, k, k, e2, CHASE_FP64);  // G' = Z^H G Z
+      hermitianize<T>(st(), k, Gp, k);
+      dbg_finite(Gp, k, k, k, sizeof(T), "G' in the refinement");
+      if (it == 2) break;
+      eig_correction<T>(st(), k, Gp, k, X, k, omega);
+      Epi e3;
+      e3.C = Wk;
+      e3.ldc = k;
+      e3.Y = Z;
+      e3.ldy = k;
+      e3.gamma = 1.0;
+      gemm(OP_N, Z, k, OP_N, X, k, k, k, k, e3, CHASE_FP64);  // Z (I + X)
+      copy_cols<T>(st(), k, k, Wk, k, Z, k);
+    }
+    // eigenvalues: diagonal of G', clusters solved exactly
+    diag_real<T>(st(), k, Gp, k, w);
+    std::vector<double> d(k);
+    CHASE_CUDA(cudaMemcpyAsync(d.data(), w, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
+    CHASE_CUDA(cudaStreamSynchronize(st()));
+    std::vector<int> cl;
+    for (int i = 0; i < k;) {
+      int j = i + 1;
+      while (j < k && std::fabs(d[j] - d[j - 1]) <= omega) ++j;
+      if (j - i > 1) {
+        if (j - i > 32) return false;
+        cl.push_back(i);
+        cl.push_back(j - i);
+      }
+      i = j;
+    }
+    const int ncl = (int)cl.size() / 2;
+    c->stats.rr_clusters += ncl;
+    if (ncl > 0) {
+      CHASE_CUDA(cudaMemcpyAsync(c->iwork, cl.data(), cl.size() * sizeof(int), cudaMemcpyHostToDevice, st()));
+      CHASE_CUDA(cudaMemsetAsync(c->status_dev, 0, sizeof(int), st()));
+      cluster_eig<T>(st(), k, ncl, c->iwork, Gp, k, Z, k, w, nullptr, c->status_dev);
+    }
+    sort_pairs<T>(st(), k, w, Z, k, Wk, c->dwork + 8, c->iwork + k);
+    return true;
+  }
+
   // ------------------------------------------------------------ Algorithm 1, lines 6-7
   // Q (n x k, ld n) orthonormal.  Out: Q <- Ritz vectors, ritz[k] ascending (device), res[k] (device).
   // Uses T2 (A Q) and Tv (n x k scratch, ld n).
@@ -382,8 +506,22 @@ template <typename T> struct Solver {
     g.ldc = k;
     gemm(OP_C, Q, n, OP_N, Wb, n, k, k, n, g, rmode);  // G = Q^H W
     hermitianize<T>(st(), k, Gb(), k);
-    T* jw = (T*)c->work;  // Jacobi workspace (k*k + 3k + 8 scalars)
-    heev_jacobi<T>(st(), k, Gb(), k, ritz, Zb(), k, jw, c->work_elems, c->dwork, c->iwork, 1e-14, 60);
+    dbg_finite(Gb(), k, k, k, sizeof(T), "the Rayleigh quotient");
+    dbg_finite(Wb, n, k, n, sizeof(T), "A Q");
+    // FP32 Jacobi + FP64-class refinement for large quotients (scratch: the Ritz-vector buffer, unused
+    // until the back-transform); the FP64 Jacobi otherwise and as the fallback
+    bool done = false;
+    if (rmode != CHASE_FP64_NATIVE && k >= 64 && n >= 3 * (int64_t)k) {
+      done = eigh_mixed(k, ritz, Tv);  // leaves G intact, so the fallback below can still use it
+      if (!done) {
+        c->stats.rr_fallbacks++;
+        if (verbose()) fprintf(stderr, "[chase] mixed eigensolve fell back to FP64 Jacobi (k=%d)\n", k);
+      }
+    }
+    if (!done) {
+      T* jw = (T*)c->work;  // Jacobi workspace (k*k + 3k + 8 scalars)
+      heev_jacobi<T>(st(), k, Gb(), k, ritz, Zb(), k, jw, c->work_elems, c->dwork, c->iwork, 1e-14, 60);
+    }
     Epi v;
     v.C = Tv;
     v.ldc = n;
@@ -742,7 +880,8 @@ static int64_t lanczos_elems(int64_t n, int runs, int steps) {
 }
 
 static int64_t work_elems_for(int64_t n, int ne, const chase_opts& o) {
-  int64_t jac = (int64_t)ne * ne + 3 * (int64_t)ne + 8;
+  // FP64 Jacobi: ne^2 + 3 ne + 8 scalars; FP32 first pass: 3 ne^2 + 3 ne + 8 half-size scalars
+  int64_t jac = 2 * (int64_t)ne * ne + 3 * (int64_t)ne + 16;
   int64_t lz = lanczos_elems(n, o.lanczos_runs, std::min<int>(o.lanczos_steps, (int)n));
   int64_t split = 2 * 1024 * 1024;
   return std::max(std::max(jac, lz), split);

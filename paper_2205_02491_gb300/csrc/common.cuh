@@ -62,6 +62,66 @@ template <> struct S<double2> {
   __host__ __device__ static inline double2 make(double r, double i) { return make_double2(r, i); }
 };
 
+// single-precision traits (FP32 first pass of the Rayleigh-Ritz eigensolve); scalars are doubles
+// at the interface and rounded to float
+template <> struct S<float> {
+  static constexpr bool cplx = false;
+  __host__ __device__ static inline float zero() { return 0.0f; }
+  __host__ __device__ static inline float one() { return 1.0f; }
+  __host__ __device__ static inline float conj(float a) { return a; }
+  __host__ __device__ static inline float mul(float a, float b) { return a * b; }
+  __host__ __device__ static inline float fma(float a, float b, float c) { return ::fmaf(a, b, c); }
+  __host__ __device__ static inline float fmac(float a, float b, float c) { return ::fmaf(a, b, c); }
+  __host__ __device__ static inline float add(float a, float b) { return a + b; }
+  __host__ __device__ static inline float sub(float a, float b) { return a - b; }
+  // scaled in double: s itself may lie outside the float range (1/|g| for a denormal g)
+  __host__ __device__ static inline float scale(float a, double s) { return (float)((double)a * s); }
+  __host__ __device__ static inline double abs2(float a) { return (double)a * (double)a; }
+  __host__ __device__ static inline double re(float a) { return a; }
+  __host__ __device__ static inline double im(float) { return 0.0; }
+  __host__ __device__ static inline float make(double r, double) { return (float)r; }
+};
+
+template <> struct S<float2> {
+  static constexpr bool cplx = true;
+  __host__ __device__ static inline float2 zero() { return make_float2(0.0f, 0.0f); }
+  __host__ __device__ static inline float2 one() { return make_float2(1.0f, 0.0f); }
+  __host__ __device__ static inline float2 conj(float2 a) { return make_float2(a.x, -a.y); }
+  __host__ __device__ static inline float2 mul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  }
+  __host__ __device__ static inline float2 fma(float2 a, float2 b, float2 c) {
+    c.x = ::fmaf(a.x, b.x, c.x);
+    c.x = ::fmaf(-a.y, b.y, c.x);
+    c.y = ::fmaf(a.x, b.y, c.y);
+    c.y = ::fmaf(a.y, b.x, c.y);
+    return c;
+  }
+  __host__ __device__ static inline float2 fmac(float2 a, float2 b, float2 c) {
+    c.x = ::fmaf(a.x, b.x, c.x);
+    c.x = ::fmaf(a.y, b.y, c.x);
+    c.y = ::fmaf(a.x, b.y, c.y);
+    c.y = ::fmaf(-a.y, b.x, c.y);
+    return c;
+  }
+  __host__ __device__ static inline float2 add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __host__ __device__ static inline float2 sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+  __host__ __device__ static inline float2 scale(float2 a, double s) {
+    return make_float2((float)((double)a.x * s), (float)((double)a.y * s));
+  }
+  __host__ __device__ static inline double abs2(float2 a) {
+    return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+  }
+  __host__ __device__ static inline double re(float2 a) { return a.x; }
+  __host__ __device__ static inline double im(float2 a) { return a.y; }
+  __host__ __device__ static inline float2 make(double r, double i) { return make_float2((float)r, (float)i); }
+};
+
+// the single-precision type used for the first pass of a FP64 type
+template <typename T> struct Lowp;
+template <> struct Lowp<double> { using type = float; };
+template <> struct Lowp<double2> { using type = float2; };
+
 // ---------------------------------------------------------------- errors
 struct Error {
   int status;

@@ -200,7 +200,7 @@ __global__ void diag_rank_kernel(int k, const T* __restrict__ G, int64_t ldg, do
 
 template <typename T>
 int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int64_t ldz, T* work, int64_t work_elems,
-                double* dwork, int* iwork, double tol, int max_sweeps) {
+                double* dwork, int* iwork, double tol, int max_sweeps, bool require_convergence) {
   // work: k*k scalars for the unsorted Z plus Rot array; dwork: 2k+2 doubles; iwork: k ints
   CHASE_REQUIRE(work_elems >= (int64_t)k * k + 3 * (int64_t)k + 8, 2, "heev_jacobi: workspace too small");
   if (k <= 0) return 0;
@@ -239,7 +239,7 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
     }
     CHASE_CHECK_LAUNCH();
   }
-  CHASE_REQUIRE(done, 8, "heev_jacobi: sweep cap reached without convergence");
+  CHASE_REQUIRE(done || !require_convergence, 8, "heev_jacobi: sweep cap reached without convergence");
   diag_rank_kernel<T><<<ceil_div(k, 128), 128, 0, st>>>(k, G, ldg, w, iwork);
   CHASE_CHECK_LAUNCH();
   permute_cols<T>(st, k, k, Zu, k, Z, ldz, iwork);
@@ -247,8 +247,12 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
 }
 
 template int heev_jacobi<double>(cudaStream_t, int, double*, int64_t, double*, double*, int64_t, double*, int64_t,
-                                 double*, int*, double, int);
+                                 double*, int*, double, int, bool);
 template int heev_jacobi<double2>(cudaStream_t, int, double2*, int64_t, double*, double2*, int64_t, double2*, int64_t,
-                                  double*, int*, double, int);
+                                  double*, int*, double, int, bool);
+template int heev_jacobi<float>(cudaStream_t, int, float*, int64_t, double*, float*, int64_t, float*, int64_t, double*,
+                                int*, double, int, bool);
+template int heev_jacobi<float2>(cudaStream_t, int, float2*, int64_t, double*, float2*, int64_t, float2*, int64_t,
+                                 double*, int*, double, int, bool);
 
 }  // namespace chase

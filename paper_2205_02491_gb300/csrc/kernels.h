@@ -51,7 +51,19 @@ template <typename T> void fro_norm2(cudaStream_t st, int64_t n, int k, const T*
 // Parallel cyclic Jacobi: G (k x k, destroyed) -> w ascending, Z.  Returns sweeps used; throws on cap.
 template <typename T>
 int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int64_t ldz, T* work,
-                int64_t work_elems, double* dwork, int* iwork, double tol, int max_sweeps);
+                int64_t work_elems, double* dwork, int* iwork, double tol, int max_sweeps,
+                bool require_convergence = true);
+
+// mixed-precision eigensolve helpers (eig_mixed.cu)
+template <typename T, typename F> void convert_mat(cudaStream_t st, int k, const T* in, int64_t ldi, F* out, int64_t ldo);
+template <typename T>
+void eig_correction(cudaStream_t st, int k, const T* Gp, int64_t ldg, T* X, int64_t ldx, double omega);
+template <typename T>
+void cluster_eig(cudaStream_t st, int k, int nclusters, const int* cl /* start,size pairs (device) */, const T* Gp,
+                 int64_t ldg, T* Z, int64_t ldz, double* w, T* scratch, int* status);
+template <typename T> void diag_real(cudaStream_t st, int k, const T* G, int64_t ldg, double* d);
+template <typename T>
+void sort_pairs(cudaStream_t st, int k, double* w, T* Z, int64_t ldz, T* tmp, double* wtmp, int* perm);
 
 // Lanczos bounds (Algorithm 1, line 2).  out4 (device) = {b_sup, mu_1, mu_ne, theta_max}.
 template <typename T>

@@ -183,3 +183,33 @@ def test_solve_c1_all_split_products(pkg, mode):
     assert np.max(np.abs(w - p.lam[:p.nev])) <= 1e-10 * nrm
     R = G.implicit_matvec(p.lam, p.U, V) - V * w[None, :]
     assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
+
+
+@pytest.mark.parametrize("cplx", [True, False])
+def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx):
+    # k >= 64 takes the FP32 Jacobi + FP64-class refinement path; include exact eigenvalue clusters
+    n, k = 900, 160
+    g = np.random.default_rng(31)
+    lam = np.sort(g.uniform(-1, 1, n))
+    lam[10:13] = lam[10]          # a triple eigenvalue inside the projected window
+    lam[40] = lam[41] + 1e-9       # a near-degenerate pair
+    lam = np.sort(lam)
+    p = G.problem_small(n, 100, 60, complex_=cplx, lam=lam, seed_pid=31)
+    A = p.dense()
+    # a basis of (nearly) the lowest eigenvectors, mixed by a random unitary so that the quotient is
+    # full; the 1e-7 perturbation moves Ritz values by ~1e-14, so the clusters survive in G
+    E = G.exact_eigvecs(p.U, np.arange(k))
+    R, _ = np.linalg.qr(p.V0[:k, :k])
+    Q, _ = np.linalg.qr(E @ R + 1e-7 * p.V0[:, :k])
+    wo, Vo = O.rayleigh_ritz(A, Q)
+    s = pkg.Chase(n, k, complex_=cplx)
+    Qt = dev(Q)
+    w, r = s.rayleigh_ritz(dev(A), Qt)
+    V = host(Qt)
+    assert np.max(np.abs(w - wo)) <= 1e-12
+    Rt = A @ V - V * w[None, :]
+    assert np.max(np.linalg.norm(Rt, axis=0) - r) <= 1e-11
+    assert np.max(np.abs(np.conj(V.T) @ V - np.eye(k))) <= 1e-12
+    st = s.stats()
+    assert st["rr_fallbacks"] == 0
+    assert st["rr_clusters"] >= 1
