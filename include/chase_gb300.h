@@ -69,6 +69,9 @@ typedef struct {
   int oz_slices;       /* FP64 mode: BF16 slices per operand, 6 or 7 (default 7) */
   int native_below_mflop; /* products below this many MFLOP use DFMA kernels; 0: always
                              split tensor-core products (default 2000) */
+  int batch_workers;   /* chase_solve_batched: problems solved concurrently, each worker with its
+                          own stream and workspace sized (n_max, ne_max); 1: one after the other
+                          on the context's stream (default 1, at most 32) */
 } chase_opts;
 
 typedef struct {
@@ -79,7 +82,8 @@ typedef struct {
   int lowp_iterations; /* outer iterations that used the mixed-precision filter */
   double ms_total, ms_lanczos, ms_filter, ms_qr, ms_rr, ms_resid;  /* stage times (CUDA events) */
   double b_sup, mu_1, mu_ne, norm_est;   /* spectral bounds after Lanczos */
-  double max_resid;    /* largest relative residual among the returned pairs */
+  double max_resid;    /* largest residual ratio abs(A v - lambda v) / norm_est over all locked pairs
+                          (computed when each pair locked; bounds the returned pairs) */
   int qr_fallbacks;    /* shifted Cholesky-QR fallbacks taken */
   int filter_launches; /* filter product launches */
   double ms_filter_kernel;      /* CUDA-event time of the FP64 split-product filter kernels alone */
@@ -121,12 +125,20 @@ int64_t chase_workspace_bytes(int64_t n_max, int ne_max, chase_dtype dtype, cons
 chase_status chase_solve(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, int nev, int nex,
                          double tol, int deg, int mode, const void* V0_dev, const void* L0_dev);
 
-/* Batched / warm-start form: nprob independent problems solved one after the
- * other with the same context (sizes <= the context's), each from its own start
- * block (warm start: pass the previous step's eigenvectors padded to nev+nex).
- * Eigenpairs are written to the caller's arrays: eigvals_dev[p] (nev[p] doubles),
- * eigvecs_dev[p] (n[p] x (nev[p]+nex[p]), ld n[p]; on exit the leading nev[p]
- * columns are the eigenvectors and the rest the next start block). */
+/* Batched / warm-start form: nprob independent problems (sizes <= the context's),
+ * each from its own start block (warm start: pass the previous step's
+ * eigenvectors padded to nev+nex).  With opts.batch_workers = W > 1 the context
+ * holds W - 1 more workspaces, each with its own non-blocking stream; W host
+ * threads take the problems in order of decreasing n (longest first) from one
+ * queue, so small problems fill the SMs that large ones leave idle.  The call
+ * first waits for the context's stream and returns when every problem has
+ * finished.  Eigenpairs are written to the caller's arrays: eigvals_dev[p]
+ * (nev[p] doubles), eigvecs_dev[p] (n[p] x (nev[p]+nex[p]), ld n[p]; on exit the
+ * leading nev[p] columns are the eigenvectors and the rest the next start
+ * block).  stats_host (nullable): nprob records.  On error the first failing
+ * problem's status is returned and the other workers stop after their current
+ * problem.  After the call, chase_eigvals/eigvecs/stats/backward refer to an
+ * unspecified problem of the batch. */
 chase_status chase_solve_batched(chase_ctx* ctx, int nprob, const void* const* A_dev, const int64_t* n,
                                  const int* nev, const int* nex, double tol, int deg, int mode,
                                  void* const* V_dev, const void* const* L0_dev, double* const* eigvals_dev,

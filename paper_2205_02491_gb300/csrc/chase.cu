@@ -9,6 +9,7 @@
 // else crosses the host-device boundary (the paper does one transfer per
 // iteration too, Section "Offloading Selected Routines to GPUs").
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -16,6 +17,8 @@
 #include <exception>
 #include <new>
 #include <string>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/chase_gb300.h"
@@ -72,6 +75,8 @@ struct chase_ctx {
   chase_stats_t stats{};
   std::string err;
   cudaEvent_t ev[8] = {};
+  // batched solves: opts.batch_workers - 1 more contexts, each with its own stream
+  std::vector<chase_ctx*> workers;
 };
 
 namespace {
@@ -93,12 +98,11 @@ struct Timer {
 };
 
 bool verbose() {
-  static int v = -1;
-  if (v < 0) {
+  static const bool v = []() {
     const char* e = getenv("CHASE_VERBOSE");
-    v = (e && e[0] && e[0] != '0') ? 1 : 0;
-  }
-  return v == 1;
+    return e && e[0] && e[0] != '0';
+  }();
+  return v;
 }
 
 void filter_coeffs(double b_sup, double mu_1, double mu_ne, int mmax, double& c, double& e, std::vector<double>& al,
@@ -427,9 +431,9 @@ template <typename T> struct Solver {
     dbg_finite(G, k, k, k, sizeof(T), "G before the FP32 pass");
     convert_mat<T, F>(st(), k, G, k, Gf, k);
     try {
-      heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40, false);
+      heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40, false, true);
     } catch (const Error& e) {
-      if (e.status != CHASE_ERR_NAN) throw;
+      if (e.status != CHASE_ERR_NAN && e.status != CHASE_ERR_TIMEOUT) throw;
       return false;  // G itself is untouched: the FP64 solver takes over
     }
     convert_mat<F, T>(st(), k, Zf, k, Z, k);
@@ -659,7 +663,18 @@ template <typename T> struct Solver {
     // Lanczos (line 2)
     {
       Timer t(c, 1, &S.ms_lanczos);
-      lanczos<T>(st(), A, n, lda, ne, L0, runs, steps, c->dwork, W(), c->work_elems, c->dwork + 8);
+      // large problems: the Lanczos matvecs use the FP64-class split tensor-core product (the digit
+      // planes of A are then reused by the filter); small ones and the native mode use DFMA
+      MatvecFn<T> mv = [&](const T* X, int64_t ldx, T* Wout) {
+        Epi e;
+        e.C = Wout;
+        e.ldc = n;
+        hemm(A, n, lda, X, ldx, runs, e, CHASE_FP64);
+      };
+      const bool lz_split = runs <= c->ne_max && use_split(mode == CHASE_FP64_NATIVE ? CHASE_FP64_NATIVE : CHASE_FP64,
+                                                           n, runs, n);
+      lanczos<T>(st(), A, n, lda, ne, L0, runs, steps, c->dwork, W(), c->work_elems, c->dwork + 8,
+                 lz_split ? &mv : nullptr);
       init_bounds_kernel<<<1, 1, 0, st()>>>(c->dwork, c->bounds);
       CHASE_CHECK_LAUNCH();
       t.stop();
@@ -697,7 +712,7 @@ template <typename T> struct Solver {
       double bnd[6];
     } hstat;
     std::vector<int> degbuf(ne);
-    std::vector<double> resbuf(ne);
+    std::vector<double> resbuf(ne), reslock(ne);
     while (l < nev && it < c->opts.maxiter) {
       ++it;
       const int k = ne - l;
@@ -744,9 +759,11 @@ template <typename T> struct Solver {
         CHASE_CUDA(cudaMemcpyAsync(hstat.bnd, c->bounds, 6 * sizeof(double), cudaMemcpyDeviceToHost, st()));
         CHASE_CUDA(cudaMemcpyAsync(degbuf.data(), c->deg, k * sizeof(int), cudaMemcpyDeviceToHost, st()));
         CHASE_CUDA(cudaMemcpyAsync(resbuf.data(), c->res2, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
+        CHASE_CUDA(cudaMemcpyAsync(reslock.data(), c->res, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
         CHASE_CUDA(cudaStreamSynchronize(st()));
         CHASE_REQUIRE(oz::read_flags(st(), c->ozw) == 0, CHASE_ERR_TIMEOUT, "a tensor-core product hit its wait limit");
         const int p = hstat.lock;
+        for (int a = 0; a < p; ++a) S.max_resid = std::max(S.max_resid, reslock[a] / norm_est);
         // lock: Ritz values of the converged prefix, then reorder the remaining active columns
         if (p > 0) CHASE_CUDA(cudaMemcpyAsync(c->lam_locked + l, c->ritz, p * sizeof(double), cudaMemcpyDeviceToDevice, st()));
         const int kr = k - p;
@@ -871,6 +888,7 @@ void chase_default_opts(chase_opts* o) {
   o->nfinal = 1;
   o->oz_slices = 7;
   o->native_below_mflop = 2000;
+  o->batch_workers = 1;
 }
 
 static int64_t lanczos_elems(int64_t n, int runs, int steps) {
@@ -907,7 +925,8 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
   chase_default_opts(&c->opts);
   if (opts) c->opts = *opts;
   if (c->opts.maxdeg < 1 || c->opts.lanczos_runs < 1 || c->opts.lanczos_runs > 8 || c->opts.lanczos_steps < 1 ||
-      c->opts.lanczos_steps > 64 || c->opts.maxiter < 1 || c->opts.oz_slices < 6 || c->opts.oz_slices > 7 || c->opts.native_below_mflop < 0) {
+      c->opts.lanczos_steps > 64 || c->opts.maxiter < 1 || c->opts.oz_slices < 6 || c->opts.oz_slices > 7 ||
+      c->opts.native_below_mflop < 0 || c->opts.batch_workers < 1 || c->opts.batch_workers > 32) {
     delete c;
     return CHASE_ERR_ARG;
   }
@@ -923,7 +942,7 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
     for (auto& e : c->ev) CHASE_CUDA(cudaEventCreate(&e));
     size_t freeb = 0, totb = 0;
     CHASE_CUDA(cudaMemGetInfo(&freeb, &totb));
-    int64_t need = chase_workspace_bytes(n_max, ne_max, dtype, &c->opts);
+    int64_t need = chase_workspace_bytes(n_max, ne_max, dtype, &c->opts) * (int64_t)c->opts.batch_workers;
     if ((size_t)need + (64ull << 20) > freeb) {
       c->err = "workspace of " + std::to_string(need) + " bytes does not fit in free device memory";
       chase_destroy(c);
@@ -953,6 +972,21 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
     CHASE_CUDA(cudaMalloc(&c->info, sizeof(int)));
     CHASE_CUDA(cudaMalloc(&c->status_dev, 4 * sizeof(int)));
     oz::create(c->ozw, n_max, ne_max, dtype == CHASE_C128, c->opts.oz_slices);
+    // workers of batched solves: same sizes and options, one non-blocking stream each
+    chase_opts wo = c->opts;
+    wo.batch_workers = 1;
+    for (int w = 1; w < c->opts.batch_workers; ++w) {
+      cudaStream_t ws = nullptr;
+      CHASE_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+      chase_ctx* wc = nullptr;
+      chase_status st = chase_create(&wc, n_max, ne_max, dtype, &wo, ws);
+      if (st != CHASE_OK) {
+        cudaStreamDestroy(ws);
+        throw chase::Error{(int)st, "creating a batch worker failed"};
+      }
+      wc->own_stream = true;
+      c->workers.push_back(wc);
+    }
   } catch (const chase::Error& e) {
     chase_destroy(c);
     return (chase_status)e.status;
@@ -963,6 +997,8 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
 
 void chase_destroy(chase_ctx* c) {
   if (!c) return;
+  for (chase_ctx* w : c->workers) chase_destroy(w);
+  c->workers.clear();
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
@@ -1135,27 +1171,79 @@ chase_status chase_perturb(chase_ctx* c, void* A, int64_t n, int64_t lda, double
   API_END(c)
 }
 
+// One problem of a batch on context c (its stream): solve, then hand back the eigenvalues and
+// the next start block (eigenvectors ascending followed by the rest of the search block).
+static void solve_one_of_batch(chase_ctx* c, const void* A, int64_t n, int nev, int nex, double tol, int deg, int mode,
+                               void* Vd, const void* L0, double* eigvals, chase_stats_t* stats) {
+  const int ne = nev + nex;
+  if (c->dtype == CHASE_C128) {
+    Solver<double2>(c).solve((const double2*)A, n, n, nev, nex, tol, deg, mode, (const double2*)Vd,
+                             (const double2*)L0);
+    copy_cols<double2>(c->stream, n, ne, (const double2*)c->T1, n, (double2*)Vd, n);
+  } else {
+    Solver<double>(c).solve((const double*)A, n, n, nev, nex, tol, deg, mode, (const double*)Vd, (const double*)L0);
+    copy_cols<double>(c->stream, n, ne, (const double*)c->T1, n, (double*)Vd, n);
+  }
+  CHASE_CUDA(cudaMemcpyAsync(eigvals, c->eigvals, nev * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  if (stats) *stats = c->stats;
+}
+
 chase_status chase_solve_batched(chase_ctx* c, int nprob, const void* const* A, const int64_t* n, const int* nev,
                                  const int* nex, double tol, int deg, int mode, void* const* Vd, const void* const* L0,
                                  double* const* eigvals, chase_stats_t* stats_host) {
   API_BEGIN(c)
   CHASE_REQUIRE(nprob >= 0 && A && n && nev && nex && Vd && L0 && eigvals, CHASE_ERR_ARG, "bad args");
-  for (int p = 0; p < nprob; ++p) {
-    int ne = nev[p] + nex[p];
-    if (c->dtype == CHASE_C128) {
-      Solver<double2> s(c);
-      s.solve((const double2*)A[p], n[p], n[p], nev[p], nex[p], tol, deg, mode, (const double2*)Vd[p],
-              (const double2*)L0[p]);
-      // eigenvectors (ascending) followed by the rest of the search block: the next start block
-      copy_cols<double2>(c->stream, n[p], ne, (const double2*)c->T1, n[p], (double2*)Vd[p], n[p]);
-    } else {
-      Solver<double> s(c);
-      s.solve((const double*)A[p], n[p], n[p], nev[p], nex[p], tol, deg, mode, (const double*)Vd[p],
-              (const double*)L0[p]);
-      copy_cols<double>(c->stream, n[p], ne, (const double*)c->T1, n[p], (double*)Vd[p], n[p]);
-    }
-    CHASE_CUDA(cudaMemcpyAsync(eigvals[p], c->eigvals, nev[p] * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    if (stats_host) stats_host[p] = c->stats;
+  if (c->workers.empty()) {
+    for (int p = 0; p < nprob; ++p)
+      solve_one_of_batch(c, A[p], n[p], nev[p], nex[p], tol, deg, mode, Vd[p], L0[p], eigvals[p],
+                         stats_host ? &stats_host[p] : nullptr);
+  } else {
+    // inputs the caller enqueued on the context's stream must be complete before the workers'
+    // non-blocking streams read them
+    CHASE_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<int> order(nprob);
+    for (int p = 0; p < nprob; ++p) order[p] = p;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    std::atomic<int> next{0};
+    std::atomic<bool> failed{false};
+    int err_status = CHASE_OK;
+    std::string err_msg;
+    std::mutex err_mu;
+    auto record = [&](int status, const std::string& msg) {
+      std::lock_guard<std::mutex> lock(err_mu);
+      if (err_status == CHASE_OK) {
+        err_status = status;
+        err_msg = msg;
+      }
+      failed.store(true);
+    };
+    auto run = [&](chase_ctx* wc) {
+      if (cudaSetDevice(wc->device) != cudaSuccess) {
+        record(CHASE_ERR_CUDA, "cudaSetDevice failed in a batch worker");
+        return;
+      }
+      for (;;) {
+        if (failed.load()) return;
+        const int i = next.fetch_add(1);
+        if (i >= nprob) return;
+        const int p = order[i];
+        try {
+          solve_one_of_batch(wc, A[p], n[p], nev[p], nex[p], tol, deg, mode, Vd[p], L0[p], eigvals[p],
+                             stats_host ? &stats_host[p] : nullptr);
+        } catch (const chase::Error& e) {
+          record(e.status, "problem " + std::to_string(p) + ": " + e.msg);
+        } catch (const std::exception& e) {
+          record(CHASE_ERR_CUDA, "problem " + std::to_string(p) + ": " + e.what());
+        }
+      }
+    };
+    std::vector<std::thread> threads;
+    threads.reserve(c->workers.size());
+    for (chase_ctx* wc : c->workers) threads.emplace_back(run, wc);
+    run(c);
+    for (auto& t : threads) t.join();
+    CHASE_REQUIRE(err_status == CHASE_OK, err_status, err_msg);
   }
   CHASE_CUDA(cudaStreamSynchronize(c->stream));
   API_END(c)

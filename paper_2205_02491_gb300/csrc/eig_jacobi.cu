@@ -8,6 +8,8 @@
 // Z (Z J).  For each pair the 2x2 block [[a, g], [conj g, b]] is made real by
 // the phase D = diag(1, conj(g)/|g|) and zeroed by the real rotation with
 // t = sign(z)/(|z| + sqrt(1+z^2)), z = (b-a)/(2|g|).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -30,11 +32,12 @@ __device__ inline void round_pair(int r, int idx, int kp, int& a, int& b) {
   }
 }
 
+// rotation parameters of pair idx of round r.  The device functions take plain (not __restrict__)
+// pointers: inside the persistent sweep kernel G and the rotations are written by other blocks
+// between barriers, so their loads must not go through the non-coherent read-only path.
 template <typename T>
-__global__ void jacobi_params_kernel(int k, int kp, int r, const T* __restrict__ G, int64_t ldg, Rot<T>* rot) {
+__device__ __forceinline__ void jacobi_params(int k, int kp, int r, int idx, const T* G, int64_t ldg, Rot<T>* rot) {
   using s = S<T>;
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= kp / 2) return;
   int a, b;
   round_pair(r, idx, kp, a, b);
   int p = min(a, b), q = max(a, b);
@@ -60,14 +63,18 @@ __global__ void jacobi_params_kernel(int k, int kp, int r, const T* __restrict__
   rot[q] = Rot<T>{p, s::scale(ph, c), s::make(sn, 0.0)};   // J[q][q], J[p][q]
 }
 
+template <typename T>
+__global__ void jacobi_params_kernel(int k, int kp, int r, const T* __restrict__ G, int64_t ldg, Rot<T>* rot) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kp / 2) return;
+  jacobi_params<T>(k, kp, r, idx, G, ldg, rot);
+}
+
 // G <- J^H G J, one thread per (row pair, column pair) 2x2 block (in place).
 template <typename T>
-__global__ void jacobi_apply_g_kernel(int k, int kp, int r, T* G, int64_t ldg, const Rot<T>* __restrict__ rot) {
+__device__ __forceinline__ void jacobi_apply_g(int k, int kp, int r, int i1, int i2, T* G, int64_t ldg,
+                                               const Rot<T>* rot) {
   using s = S<T>;
-  int i1 = blockIdx.x * blockDim.x + threadIdx.x;  // row pair index
-  int i2 = blockIdx.y * blockDim.y + threadIdx.y;  // column pair index
-  int half = kp / 2;
-  if (i1 >= half || i2 >= half) return;
   int a, b, c, d;
   round_pair(r, i1, kp, a, b);
   round_pair(r, i2, kp, c, d);
@@ -118,13 +125,20 @@ __global__ void jacobi_apply_g_kernel(int k, int kp, int r, T* G, int64_t ldg, c
     }
 }
 
+template <typename T>
+__global__ void jacobi_apply_g_kernel(int k, int kp, int r, T* G, int64_t ldg, const Rot<T>* __restrict__ rot) {
+  int i1 = blockIdx.x * blockDim.x + threadIdx.x;  // row pair index
+  int i2 = blockIdx.y * blockDim.y + threadIdx.y;  // column pair index
+  int half = kp / 2;
+  if (i1 >= half || i2 >= half) return;
+  jacobi_apply_g<T>(k, kp, r, i1, i2, G, ldg, rot);
+}
+
 // Z <- Z J (rows i, column pairs), in place.
 template <typename T>
-__global__ void jacobi_apply_z_kernel(int k, int kp, int r, T* Z, int64_t ldz, const Rot<T>* __restrict__ rot) {
+__device__ __forceinline__ void jacobi_apply_z(int k, int kp, int r, int i, int pi, T* Z, int64_t ldz,
+                                               const Rot<T>* rot) {
   using s = S<T>;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int pi = blockIdx.y;
-  if (i >= k) return;
   int a, b;
   round_pair(r, pi, kp, a, b);
   if (a >= k || b >= k) return;
@@ -132,6 +146,93 @@ __global__ void jacobi_apply_z_kernel(int k, int kp, int r, T* Z, int64_t ldz, c
   T za = Z[i + (int64_t)a * ldz], zb = Z[i + (int64_t)b * ldz];
   Z[i + (int64_t)a * ldz] = s::add(s::mul(za, ra.self), s::mul(zb, ra.other));
   Z[i + (int64_t)b * ldz] = s::add(s::mul(zb, rb.self), s::mul(za, rb.other));
+}
+
+template <typename T>
+__global__ void jacobi_apply_z_kernel(int k, int kp, int r, T* Z, int64_t ldz, const Rot<T>* __restrict__ rot) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int pi = blockIdx.y;
+  if (i >= k) return;
+  jacobi_apply_z<T>(k, kp, r, i, pi, Z, ldz, rot);
+}
+
+// ---------------------------------------------------------------- persistent sweep
+// One cooperative launch runs all kp-1 rounds of a sweep: rotation parameters, then the G and Z
+// updates, separated by grid-wide barriers (all blocks are co-resident under a cooperative
+// launch).  Every barrier wait is bounded by a wall-clock limit; on expiry, or when another block
+// has flagged an error, the block sets/keeps the error flag and returns.
+constexpr unsigned long long GRID_WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bar[0]: arrivals, bar[1]: generation, bar[2]: error flag (all zero at launch)
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vb = bar;
+    int ok = vb[2] == 0u;
+    if (ok) {
+      const unsigned gen = vb[1];
+      __threadfence();
+      if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
+        atomicExch(&bar[0], 0u);
+        __threadfence();
+        atomicAdd(&bar[1], 1u);
+      } else {
+        const unsigned long long t0 = gtimer();
+        while (vb[1] == gen) {
+          if (vb[2] != 0u) {
+            ok = 0;
+            break;
+          }
+          if (gtimer() - t0 > GRID_WAIT_NS) {
+            atomicOr(&bar[2], 1u);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+    }
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) jacobi_sweep_kernel(int k, int kp, T* G, int64_t ldg, T* Z, int64_t ldz,
+                                                           Rot<T>* rot, unsigned* bar) {
+  const int half = kp / 2;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t ng = (int64_t)half * half, nz = (int64_t)k * half;
+  for (int r = 0; r < kp - 1; ++r) {
+    for (int64_t idx = tid; idx < half; idx += nthr) jacobi_params<T>(k, kp, r, (int)idx, G, ldg, rot);
+    if (!grid_barrier(bar, gridDim.x)) return;
+    for (int64_t x = tid; x < ng; x += nthr) jacobi_apply_g<T>(k, kp, r, (int)(x % half), (int)(x / half), G, ldg, rot);
+    for (int64_t x = tid; x < nz; x += nthr) jacobi_apply_z<T>(k, kp, r, (int)(x % k), (int)(x / k), Z, ldz, rot);
+    if (!grid_barrier(bar, gridDim.x)) return;
+  }
+}
+
+// blocks of 256 threads that can be co-resident for the sweep kernel (0: no cooperative launch)
+template <typename T> static int sweep_grid() {
+  static const int nb = []() {
+    int dev = 0, sms = 0, per = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_sweep_kernel<T>, 256, 0) != cudaSuccess) return 0;
+    return sms * std::min(per, 4);
+  }();
+  return nb;
 }
 
 template <typename T> __global__ void set_identity_kernel(int k, T* Z, int64_t ldz) {
@@ -200,7 +301,7 @@ __global__ void diag_rank_kernel(int k, const T* __restrict__ G, int64_t ldg, do
 
 template <typename T>
 int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int64_t ldz, T* work, int64_t work_elems,
-                double* dwork, int* iwork, double tol, int max_sweeps, bool require_convergence) {
+                double* dwork, int* iwork, double tol, int max_sweeps, bool require_convergence, bool persistent) {
   // work: k*k scalars for the unsorted Z plus Rot array; dwork: 2k+2 doubles; iwork: k ints
   CHASE_REQUIRE(work_elems >= (int64_t)k * k + 3 * (int64_t)k + 8, 2, "heev_jacobi: workspace too small");
   if (k <= 0) return 0;
@@ -213,13 +314,20 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
   double hstat[2];
   int sweeps = 0;
   bool done = false;
+  // one cooperative launch per sweep; the barrier words live in iwork (overwritten by the final
+  // ranking only after the sweeps)
+  const int coop_grid = (persistent && k >= 64) ? sweep_grid<T>() : 0;
+  unsigned* bar = reinterpret_cast<unsigned*>(iwork);
+  unsigned bar_err = 0;
   for (; sweeps <= max_sweeps; ++sweeps) {
     offdiag_partial_kernel<T><<<k, 128, 0, st>>>(k, G, ldg, part);
     CHASE_CHECK_LAUNCH();
     offdiag_sum_kernel<<<1, 32, 0, st>>>(k, part, dwork);
     CHASE_CHECK_LAUNCH();
     CHASE_CUDA(cudaMemcpyAsync(hstat, dwork, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (coop_grid > 0 && sweeps > 0) CHASE_CUDA(cudaMemcpyAsync(&bar_err, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CHASE_CUDA(cudaStreamSynchronize(st));
+    CHASE_REQUIRE(bar_err == 0, 8, "heev_jacobi: a grid barrier of the sweep kernel hit its wait limit");
     CHASE_REQUIRE(isfinite(hstat[0]) && isfinite(hstat[1]), 5, "heev_jacobi: non-finite matrix");
     if (sqrt(hstat[0]) <= tol * sqrt(hstat[1]) || k == 1) {
       done = true;
@@ -229,15 +337,26 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
     int half = kp / 2;
     dim3 gblk(16, 16), ggrid(ceil_div(half, 16), ceil_div(half, 16));
     dim3 zgrid(ceil_div(k, 128), half);
-    for (int r = 0; r < kp - 1; ++r) {
-      jacobi_params_kernel<T><<<ceil_div(half, 128), 128, 0, st>>>(k, kp, r, G, ldg, rot);
+    if (coop_grid > 0) {
+      CHASE_CUDA(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
+      int kk = k, kpp = kp;
+      int64_t ldgg = ldg, ldzz = k;
+      T* Gp = G;
+      T* Zp = Zu;
+      Rot<T>* rp = rot;
+      void* args[] = {&kk, &kpp, &Gp, &ldgg, &Zp, &ldzz, &rp, &bar};
+      CHASE_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel<T>, dim3(coop_grid), dim3(256), args, 0, st));
       CHASE_CHECK_LAUNCH();
-      jacobi_apply_g_kernel<T><<<ggrid, gblk, 0, st>>>(k, kp, r, G, ldg, rot);
-      CHASE_CHECK_LAUNCH();
-      jacobi_apply_z_kernel<T><<<zgrid, 128, 0, st>>>(k, kp, r, Zu, k, rot);
-      CHASE_CHECK_LAUNCH();
+    } else {
+      for (int r = 0; r < kp - 1; ++r) {
+        jacobi_params_kernel<T><<<ceil_div(half, 128), 128, 0, st>>>(k, kp, r, G, ldg, rot);
+        CHASE_CHECK_LAUNCH();
+        jacobi_apply_g_kernel<T><<<ggrid, gblk, 0, st>>>(k, kp, r, G, ldg, rot);
+        CHASE_CHECK_LAUNCH();
+        jacobi_apply_z_kernel<T><<<zgrid, 128, 0, st>>>(k, kp, r, Zu, k, rot);
+        CHASE_CHECK_LAUNCH();
+      }
     }
-    CHASE_CHECK_LAUNCH();
   }
   CHASE_REQUIRE(done || !require_convergence, 8, "heev_jacobi: sweep cap reached without convergence");
   diag_rank_kernel<T><<<ceil_div(k, 128), 128, 0, st>>>(k, G, ldg, w, iwork);
@@ -247,12 +366,12 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
 }
 
 template int heev_jacobi<double>(cudaStream_t, int, double*, int64_t, double*, double*, int64_t, double*, int64_t,
-                                 double*, int*, double, int, bool);
+                                 double*, int*, double, int, bool, bool);
 template int heev_jacobi<double2>(cudaStream_t, int, double2*, int64_t, double*, double2*, int64_t, double2*, int64_t,
-                                  double*, int*, double, int, bool);
+                                  double*, int*, double, int, bool, bool);
 template int heev_jacobi<float>(cudaStream_t, int, float*, int64_t, double*, float*, int64_t, float*, int64_t, double*,
-                                int*, double, int, bool);
+                                int*, double, int, bool, bool);
 template int heev_jacobi<float2>(cudaStream_t, int, float2*, int64_t, double*, float2*, int64_t, float2*, int64_t,
-                                 double*, int*, double, int, bool);
+                                 double*, int*, double, int, bool, bool);
 
 }  // namespace chase

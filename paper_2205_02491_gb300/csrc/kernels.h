@@ -1,5 +1,6 @@
 // Internal launch interface of the FP64 kernels (host side).  Not part of the C ABI.
 #pragma once
+#include <functional>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,7 +53,7 @@ template <typename T> void fro_norm2(cudaStream_t st, int64_t n, int k, const T*
 template <typename T>
 int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int64_t ldz, T* work,
                 int64_t work_elems, double* dwork, int* iwork, double tol, int max_sweeps,
-                bool require_convergence = true);
+                bool require_convergence = true, bool persistent = false);
 
 // mixed-precision eigensolve helpers (eig_mixed.cu)
 template <typename T, typename F> void convert_mat(cudaStream_t st, int k, const T* in, int64_t ldi, F* out, int64_t ldo);
@@ -66,9 +67,12 @@ template <typename T>
 void sort_pairs(cudaStream_t st, int k, double* w, T* Z, int64_t ldz, T* tmp, double* wtmp, int* perm);
 
 // Lanczos bounds (Algorithm 1, line 2).  out4 (device) = {b_sup, mu_1, mu_ne, theta_max}.
+// matvec (nullable): W (n x runs, ld n) = A X (X: n x runs, ld ldx) on stream st, replacing the
+// DFMA multi-vector HEMV (used with the FP64-class split tensor-core products).
+template <typename T> using MatvecFn = std::function<void(const T* X, int64_t ldx, T* W)>;
 template <typename T>
 void lanczos(cudaStream_t st, const T* A, int64_t n, int64_t lda, int ne, const T* L0, int runs, int steps,
-             double* out4, T* work, int64_t work_elems, double* dwork);
+             double* out4, T* work, int64_t work_elems, double* dwork, const MatvecFn<T>* matvec = nullptr);
 
 // Input generator from compact-WY factors.
 template <typename T>

@@ -1,7 +1,8 @@
 // Lanczos spectral-bound estimation (Algorithm 1, line 2) on the device.
 //
 // All runs advance together: a multi-vector HEMV (A times one vector per run,
-// FP64, A streamed once per step), the three-term update, one classical
+// FP64 DFMA with A streamed once per step, or the caller's FP64-class split
+// tensor-core product for large n), the three-term update, one classical
 // Gram-Schmidt reorthogonalisation against the run's basis, normalisation.  The
 // tridiagonal T of each run is diagonalised by a single-block cyclic Jacobi
 // (same rotation as the Rayleigh-Ritz solver), and one thread computes
@@ -313,7 +314,7 @@ __global__ void lanczos_bounds_kernel(int runs, int steps, int64_t n, int ne, co
 
 template <typename T>
 void lanczos(cudaStream_t st, const T* A, int64_t n, int64_t lda, int ne, const T* L0, int runs, int steps,
-             double* out4, T* work, int64_t work_elems, double* dwork) {
+             double* out4, T* work, int64_t work_elems, double* dwork, const MatvecFn<T>* matvec) {
   CHASE_REQUIRE(runs >= 1 && runs <= LZ_MAXR, 1, "lanczos: 1 <= runs <= 8");
   CHASE_REQUIRE(steps >= 1 && steps <= LZ_MAXS && steps <= n, 1, "lanczos: 1 <= steps <= min(64, n)");
   int64_t nchunk = ceil_div(n, HEMV_COLS);
@@ -342,15 +343,19 @@ void lanczos(cudaStream_t st, const T* A, int64_t n, int64_t lda, int ne, const 
   // "ldx" between runs is n*steps.
   for (int j = 0; j < steps; ++j) {
     const T* X = Vb + (int64_t)j * n;
-    dim3 g1(ceil_div(n, HEMV_ROWS), nchunk);
-    switch (runs) {
+    if (matvec) {
+      (*matvec)(X, n * steps, W);
+    } else {
+      dim3 g1(ceil_div(n, HEMV_ROWS), nchunk);
+      switch (runs) {
 #define CASE(R) case R: hemv_multi_kernel<T, R><<<g1, HEMV_ROWS, 0, st>>>(n, A, lda, X, n * steps, part); break;
-      CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
+      }
+      CHASE_CHECK_LAUNCH();
+      hemv_reduce_kernel<T><<<ceil_div(n * runs, 256), 256, 0, st>>>(n, runs, (int)nchunk, part, W, n);
+      CHASE_CHECK_LAUNCH();
     }
-    CHASE_CHECK_LAUNCH();
-    hemv_reduce_kernel<T><<<ceil_div(n * runs, 256), 256, 0, st>>>(n, runs, (int)nchunk, part, W, n);
-    CHASE_CHECK_LAUNCH();
     int m = j + 1;
     // alpha_j and the three-term update
     basis_dots_kernel<T><<<dim3(DOT_CHUNKS, runs), 256, 0, st>>>(n, m, steps, Vb, W, part);
@@ -378,8 +383,8 @@ void lanczos(cudaStream_t st, const T* A, int64_t n, int64_t lda, int ne, const 
 }
 
 template void lanczos<double>(cudaStream_t, const double*, int64_t, int64_t, int, const double*, int, int, double*,
-                              double*, int64_t, double*);
+                              double*, int64_t, double*, const MatvecFn<double>*);
 template void lanczos<double2>(cudaStream_t, const double2*, int64_t, int64_t, int, const double2*, int, int, double*,
-                               double2*, int64_t, double*);
+                               double2*, int64_t, double*, const MatvecFn<double2>*);
 
 }  // namespace chase

@@ -220,6 +220,7 @@ struct EpiArgs {
 // first MMAs of every k-block go to the inexact accumulator while the epilogue
 // flushes the exact ones
 template <int S, int NEX, bool CPLX>
+// 168 registers: ten warps put three on some SM sub-partitions (16384 registers each)
 __global__ void __maxnreg__(168)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, const double* __restrict__ a_scale, const double* __restrict__ b_scale, EpiArgs ep,
@@ -382,7 +383,8 @@ __global__ void __maxnreg__(168)
         a_iter += S;
       } else {
         // first k-block of a chunk: every inexact pair of the k-block runs while the epilogue
-        // flushes the exact accumulators of the previous chunk, then the exact pairs
+        // flushes the exact accumulators of the previous chunk, then the exact pairs.  Slices
+        // t >= NEX have no exact pairs (level t + u >= NEX): their slots are released at once.
 #pragma unroll
         for (int ti = 0; ti < S; ++ti) {
           const int as = (a_iter + ti) % Cf::A_SLOTS;
@@ -390,12 +392,14 @@ __global__ void __maxnreg__(168)
           if (!ok) break;
           fence_after();
           issue_slice(S - 1 - ti, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
+          if (S - 1 - ti >= NEX) mma_commit(smem_u32(&a_empty[as]));
         }
         if (ok && !mbar_wait(smem_u32(tmem_empty), (chunk - 1) & 1, abort_sh, err)) ok = false;
         if (!ok) break;
         fence_after();
 #pragma unroll
         for (int ti = 0; ti < S; ++ti) {
+          if (S - 1 - ti >= NEX) continue;
           const int as = (a_iter + ti) % Cf::A_SLOTS;
           issue_slice(S - 1 - ti, 2, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
           mma_commit(smem_u32(&a_empty[as]));
@@ -661,15 +665,15 @@ static int slices_for(int mode, int fp64_slices) {
 static int64_t kpad(int64_t K) { return (K + 7) / 8 * 8; }
 
 bool available() {
-  static int ok = -1;
-  if (ok < 0) {
+  // thread-safe one-time probe (batched solves call this from several host threads)
+  static const bool ok = []() {
     int dev = 0, major = 0, minor = 0;
-    ok = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
-      ok = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
-  }
-  return ok == 1;
+    return cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess && major == 10 &&
+           minor == 3 && encode_fn() != nullptr;
+  }();
+  return ok;
 }
 
 static int64_t left_elems(int64_t n_max, int ne_max) {
@@ -807,12 +811,14 @@ static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double*
   const int ap = CPLX ? 2 : 1, bp = CPLX ? 3 : 1;
   CUtensorMap ma = make_map(lpl, K, kp, M, l_slices_total * ap, BM);
   CUtensorMap mb = make_map(rpl, K, kp, N, S * bp, Cf::BROWS);
-  static bool attr_set = false;
-  if (!attr_set) {
-    CHASE_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    Cf::SMEM_BYTES));
-    attr_set = true;
-  }
+  // once per instantiation, thread-safe (batched solves launch from several host threads)
+  static std::once_flag attr_once;
+  cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&]() {
+    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Cf::SMEM_BYTES);
+  });
+  CHASE_CUDA(attr_err);
   EpiArgs ea{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
   dim3 grid(ceil_div(N, Cf::NCOLS), ceil_div(M, BM));
   CHASE_REQUIRE(grid.y <= 65535, 1, "split product: M too large");

@@ -58,3 +58,43 @@ def test_batched_warm_start_sequence(pkg):
     # warm starts from the previous eigenvectors need fewer filter products than the cold start
     for q in range(len(probs)):
         assert max(mv[1][q], mv[2][q]) < mv[0][q]
+
+
+@pytest.mark.parametrize("workers", [1, 3])
+def test_batched_workers_uneven_sizes(pkg, workers):
+    """Concurrent workers (one stream and workspace each) solve a batch of uneven sizes; every problem
+    meets the eigenvalue and residual tolerance against a dense eigendecomposition, and the returned
+    start blocks warm-start a second, perturbed step."""
+    ns = [160, 613, 96, 401, 257, 520, 333]
+    probs = [G.problem_c4(pid, n) for pid, n in enumerate(ns)]
+    ctx = pkg.Chase(max(ns), max(p.ne for p in probs), complex_=True, opts={"batch_workers": workers})
+    A_host = [p.dense() for p in probs]
+    A_dev = [dev(a) for a in A_host]
+    V = [dev(p.V0) for p in probs]
+    L0 = [dev(p.L0) for p in probs]
+    for step in range(2):
+        ws, stats = ctx.solve_batched(A_dev, [p.nev for p in probs], [p.nex for p in probs], 1e-10, 20, "fp64", V, L0)
+        for q, p in enumerate(probs):
+            lam_all = np.linalg.eigvalsh(A_host[q])
+            nrm = np.max(np.abs(lam_all))
+            w = ws[q].cpu().numpy()
+            assert np.max(np.abs(w - lam_all[: p.nev])) <= 1e-10 * nrm
+            Vq = host(V[q])[:, : p.nev]
+            R = A_host[q] @ Vq - Vq * w[None, :]
+            assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
+            assert stats[q]["locked"] >= p.nev and 0.0 < stats[q]["max_resid"] <= 1e-10
+        for q, p in enumerate(probs):
+            seed = G.sequence_seed(q, step)
+            ctx.perturb(A_dev[q], 1e-3, seed)
+            A_host[q] = A_host[q] + 1e-3 * G.perturbation(p.n, seed, True)
+    ctx.close()
+
+
+def test_batched_rejects_oversize_problem(pkg):
+    """A problem larger than the context is an argument error, reported as a status (no device work)."""
+    ctx = pkg.Chase(128, 12, complex_=True, opts={"batch_workers": 2})
+    p = G.problem_c4(0, 200)
+    with pytest.raises(pkg.ChaseError) as e:
+        ctx.solve_batched([dev(p.dense())], [p.nev], [p.nex], 1e-10, 20, "fp64", [dev(p.V0)], [dev(p.L0)])
+    assert e.value.status == 1
+    ctx.close()

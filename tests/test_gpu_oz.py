@@ -185,10 +185,11 @@ def test_solve_c1_all_split_products(pkg, mode):
     assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
 
 
-@pytest.mark.parametrize("cplx", [True, False])
-def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx):
-    # k >= 64 takes the FP32 Jacobi + FP64-class refinement path; include exact eigenvalue clusters
-    n, k = 900, 160
+@pytest.mark.parametrize("cplx,k", [(True, 160), (False, 160), (True, 97)])
+def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx, k):
+    # k >= 64 takes the FP32 Jacobi (one cooperative launch per sweep) + FP64-class refinement path;
+    # include exact eigenvalue clusters; odd k exercises the dummy index of the round-robin order
+    n = 900
     g = np.random.default_rng(31)
     lam = np.sort(g.uniform(-1, 1, n))
     lam[10:13] = lam[10]          # a triple eigenvalue inside the projected window
