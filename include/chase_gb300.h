@@ -116,14 +116,20 @@ const char* chase_last_error(const chase_ctx* ctx);
  * caller's) plus split-product buffers. */
 int64_t chase_workspace_bytes(int64_t n_max, int ne_max, chase_dtype dtype, const chase_opts* opts);
 
-/* Algorithm 1 end to end.  A_dev: n x n Hermitian (lda >= n).  V0_dev: optional
- * n x (nev+nex) start block (ld n); NULL is an error in this build: the caller
- * supplies the random block.  L0_dev: n x lanczos_runs Lanczos start vectors (ld n).
+/* Algorithm 1 end to end.  A: n x n Hermitian (lda >= n).  V0: n x (nev+nex)
+ * start block (ld n); the caller supplies the random block (NULL is an error).
+ * L0: n x lanczos_runs Lanczos start vectors (ld n).
+ * A, V0 and L0 may be device pointers or host pointers (pinned or pageable):
+ * host inputs are first copied to the device on the context's stream (pinned
+ * memory is copied by DMA).  A host A needs a device copy of n x n elements,
+ * allocated on the first such call and kept until chase_destroy
+ * (CHASE_ERR_OOM if it does not fit).
  * Converged when the residual of each of the nev lowest Ritz pairs is
  * <= tol * ||A||_est (||A||_est: largest Lanczos Ritz value magnitude).
- * Synchronous: returns when the solve has finished. */
-chase_status chase_solve(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t lda, int nev, int nex,
-                         double tol, int deg, int mode, const void* V0_dev, const void* L0_dev);
+ * Synchronous: returns when the solve has finished; read the results with
+ * chase_eigvals / chase_eigvecs (to host or device memory). */
+chase_status chase_solve(chase_ctx* ctx, const void* A, int64_t n, int64_t lda, int nev, int nex,
+                         double tol, int deg, int mode, const void* V0, const void* L0);
 
 /* Batched / warm-start form: nprob independent problems (sizes <= the context's),
  * each from its own start block (warm start: pass the previous step's

@@ -73,16 +73,19 @@ class Chase:
               V0t: torch.Tensor | None = None, L0t: torch.Tensor | None = None):
         """At: column-major storage (n x n) of A; V0t: (ne x n) storage of V0; L0t: (runs x n).
 
-        Returns (eigvals[nev] float64 cuda, eigvecs storage (nev x n), i.e. eigvecs = result.mT).
+        The inputs may be CUDA tensors or CPU tensors (pinned for DMA speed): the library copies host inputs
+        to the device itself.  Returns (eigvals[nev] float64, eigvecs storage (nev x n), i.e. eigvecs =
+        result.mT), on At's device.
         """
         n = At.shape[-1]
         mode = L.MODES[mode] if isinstance(mode, str) else int(mode)
         self._chk(self.lib.chase_solve(self.ctx, _ptr(At), n, n, nev, nex, float(tol), int(deg), mode, _ptr(V0t),
                                        _ptr(L0t)))
+        on_dev = 1 if At.is_cuda else 0
         w = torch.empty(nev, dtype=torch.float64, device=At.device)
         Vt = torch.empty((nev, n), dtype=self.dtype, device=At.device)
-        self._chk(self.lib.chase_eigvals(self.ctx, _ptr(w), 1))
-        self._chk(self.lib.chase_eigvecs(self.ctx, _ptr(Vt), n, 1))
+        self._chk(self.lib.chase_eigvals(self.ctx, _ptr(w), on_dev))
+        self._chk(self.lib.chase_eigvecs(self.ctx, _ptr(Vt), n, on_dev))
         return w, Vt
 
     def stats(self) -> dict:

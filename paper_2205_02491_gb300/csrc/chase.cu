@@ -62,6 +62,9 @@ struct chase_ctx {
   double* lam_sorted = nullptr;  // all locked eigenvalues of the last solve, ascending
   int l_final = 0;               // locked pairs of the last solve
   double* bwd = nullptr;         // adjoint work: 9 blocks n x nev (allocated on first backward)
+  void* a_stage = nullptr;       // device copy of a host A (allocated on the first solve given one)
+  size_t a_stage_bytes = 0;
+  void* l0_stage = nullptr;      // device copy of host Lanczos start vectors (n_max x 8)
   size_t bwd_bytes = 0;
   int* deg = nullptr;
   int* perm = nullptr;
@@ -1003,7 +1006,7 @@ void chase_destroy(chase_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
                   c->lam_locked, c->eigvals, c->lam_sorted, c->bwd, c->bounds, c->deg, c->perm, c->info,
-                  c->status_dev};
+                  c->status_dev, c->a_stage, c->l0_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   oz::destroy(c->ozw);
@@ -1017,9 +1020,52 @@ const char* chase_last_error(const chase_ctx* c) { return c ? c->err.c_str() : "
 
 int64_t chase_kernel_launch_count(void) { return (int64_t)chase::g_kernel_launches.load(); }
 
+// true for memory the device cannot be handed directly as a kernel argument of this library:
+// pageable or pinned host allocations (copied to the device first)
+static bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer is plain host memory
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
 chase_status chase_solve(chase_ctx* c, const void* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg,
                          int mode, const void* V0, const void* L0) {
   API_BEGIN(c)
+  CHASE_REQUIRE(A && V0 && L0, CHASE_ERR_ARG, "null A, V0 or L0");
+  CHASE_REQUIRE(n >= 1 && n <= c->n_max && lda >= n, CHASE_ERR_ARG, "n or lda out of range for this context");
+  CHASE_REQUIRE(nev >= 1 && nex >= 0 && nev + nex <= c->ne_max, CHASE_ERR_ARG, "nev/nex out of range");
+  // host inputs: copied to the device on the context's stream (pinned memory: DMA at link speed)
+  const size_t esz = c->esz;
+  if (is_host_ptr(A)) {
+    const size_t need = (size_t)n * (size_t)n * esz;
+    if (c->a_stage_bytes < need) {
+      if (c->a_stage) CHASE_CUDA(cudaFree(c->a_stage));
+      c->a_stage = nullptr;
+      c->a_stage_bytes = 0;
+      size_t freeb = 0, totb = 0;
+      CHASE_CUDA(cudaMemGetInfo(&freeb, &totb));
+      CHASE_REQUIRE(need + (64ull << 20) <= freeb, CHASE_ERR_OOM, "no device memory for a copy of the host A");
+      CHASE_CUDA(cudaMalloc(&c->a_stage, need));
+      c->a_stage_bytes = need;
+    }
+    CHASE_CUDA(cudaMemcpy2DAsync(c->a_stage, n * esz, A, lda * esz, n * esz, n, cudaMemcpyHostToDevice, c->stream));
+    A = c->a_stage;
+    lda = n;
+  }
+  if (is_host_ptr(V0)) {
+    // the filter partner buffer is free until the first filter step (V0 is read before it)
+    CHASE_CUDA(cudaMemcpyAsync(c->T1, V0, (size_t)n * (nev + nex) * esz, cudaMemcpyHostToDevice, c->stream));
+    V0 = c->T1;
+  }
+  if (is_host_ptr(L0)) {
+    if (!c->l0_stage) CHASE_CUDA(cudaMalloc(&c->l0_stage, (size_t)c->n_max * 8 * esz));
+    CHASE_CUDA(cudaMemcpyAsync(c->l0_stage, L0, (size_t)n * c->opts.lanczos_runs * esz, cudaMemcpyHostToDevice,
+                               c->stream));
+    L0 = c->l0_stage;
+  }
   if (c->dtype == CHASE_C128)
     Solver<double2>(c).solve((const double2*)A, n, lda, nev, nex, tol, deg, mode, (const double2*)V0, (const double2*)L0);
   else

@@ -70,59 +70,76 @@ __global__ void jacobi_params_kernel(int k, int kp, int r, const T* __restrict__
   jacobi_params<T>(k, kp, r, idx, G, ldg, rot);
 }
 
-// G <- J^H G J, one thread per (row pair, column pair) 2x2 block (in place).
+// G <- J^H G J, one thread per (row pair, column pair) 2x2 block (in place).  Split into a load
+// and a compute/store half so that the persistent sweep can keep several blocks' loads in flight.
+template <typename T> struct GItem {
+  int rows[2], cols[2];
+  bool diag;  // i1 == i2: the rotated pair's own 2x2 block
+  T in[2][2], js[2], jo[2], ks[2], ko[2];
+};
+
 template <typename T>
-__device__ __forceinline__ void jacobi_apply_g(int k, int kp, int r, int i1, int i2, T* G, int64_t ldg,
-                                               const Rot<T>* rot) {
+__device__ __forceinline__ void g_load(int k, int kp, int r, int i1, int i2, const T* G, int64_t ldg,
+                                       const Rot<T>* rot, GItem<T>& it) {
   using s = S<T>;
-  int a, b, c, d;
-  round_pair(r, i1, kp, a, b);
-  round_pair(r, i2, kp, c, d);
-  int rows[2] = {a, b}, cols[2] = {c, d};
-  T in[2][2];
+  round_pair(r, i1, kp, it.rows[0], it.rows[1]);
+  round_pair(r, i2, kp, it.cols[0], it.cols[1]);
+  it.diag = i1 == i2;
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int v = 0; v < 2; ++v)
-      in[u][v] = (rows[u] < k && cols[v] < k) ? G[rows[u] + (int64_t)cols[v] * ldg] : s::zero();
+      it.in[u][v] = (it.rows[u] < k && it.cols[v] < k) ? G[it.rows[u] + (int64_t)it.cols[v] * ldg] : s::zero();
   // coefficients: J[x][x] and J[partner(x)][x]
-  T js[2], jo[2], ks[2], ko[2];
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
-    if (rows[u] < k) {
-      Rot<T> rr = rot[rows[u]];
-      js[u] = rr.self;
-      jo[u] = rr.partner >= 0 ? rr.other : s::zero();
+    if (it.rows[u] < k) {
+      Rot<T> rr = rot[it.rows[u]];
+      it.js[u] = rr.self;
+      it.jo[u] = rr.partner >= 0 ? rr.other : s::zero();
     } else {
-      js[u] = s::one();
-      jo[u] = s::zero();
+      it.js[u] = s::one();
+      it.jo[u] = s::zero();
     }
-    if (cols[u] < k) {
-      Rot<T> rc = rot[cols[u]];
-      ks[u] = rc.self;
-      ko[u] = rc.partner >= 0 ? rc.other : s::zero();
+    if (it.cols[u] < k) {
+      Rot<T> rc = rot[it.cols[u]];
+      it.ks[u] = rc.self;
+      it.ko[u] = rc.partner >= 0 ? rc.other : s::zero();
     } else {
-      ks[u] = s::one();
-      ko[u] = s::zero();
+      it.ks[u] = s::one();
+      it.ko[u] = s::zero();
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void g_store(int k, T* G, int64_t ldg, const GItem<T>& it) {
+  using s = S<T>;
   // column update: C[u][v] = in[u][v] J[v][v] + in[u][v'] J[v'][v]
   T cu[2][2];
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 2; ++v) cu[u][v] = s::add(s::mul(in[u][v], ks[v]), s::mul(in[u][1 - v], ko[v]));
+    for (int v = 0; v < 2; ++v) cu[u][v] = s::add(s::mul(it.in[u][v], it.ks[v]), s::mul(it.in[u][1 - v], it.ko[v]));
   // row update: out[u][v] = conj(J[u][u]) C[u][v] + conj(J[u'][u]) C[u'][v]
 #pragma unroll
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      if (rows[u] >= k || cols[v] >= k) continue;
-      T o = s::add(s::mul(s::conj(js[u]), cu[u][v]), s::mul(s::conj(jo[u]), cu[1 - u][v]));
-      if (rows[u] == cols[v]) o = s::make(s::re(o), 0.0);
-      if (i1 == i2 && u != v) o = s::zero();  // the rotated pair's off-diagonal entry
-      G[rows[u] + (int64_t)cols[v] * ldg] = o;
+      if (it.rows[u] >= k || it.cols[v] >= k) continue;
+      T o = s::add(s::mul(s::conj(it.js[u]), cu[u][v]), s::mul(s::conj(it.jo[u]), cu[1 - u][v]));
+      if (it.rows[u] == it.cols[v]) o = s::make(s::re(o), 0.0);
+      if (it.diag && u != v) o = s::zero();  // the rotated pair's off-diagonal entry
+      G[it.rows[u] + (int64_t)it.cols[v] * ldg] = o;
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void jacobi_apply_g(int k, int kp, int r, int i1, int i2, T* G, int64_t ldg,
+                                               const Rot<T>* rot) {
+  GItem<T> it;
+  g_load<T>(k, kp, r, i1, i2, G, ldg, rot, it);
+  g_store<T>(k, G, ldg, it);
 }
 
 template <typename T>
@@ -134,18 +151,38 @@ __global__ void jacobi_apply_g_kernel(int k, int kp, int r, T* G, int64_t ldg, c
   jacobi_apply_g<T>(k, kp, r, i1, i2, G, ldg, rot);
 }
 
-// Z <- Z J (rows i, column pairs), in place.
+// Z <- Z J (rows i, column pairs), in place; load / compute-store halves as for G.
+template <typename T> struct ZItem {
+  int a, b;
+  T za, zb, as, ao, bs, bo;
+};
+
+template <typename T>
+__device__ __forceinline__ bool z_load(int k, int kp, int r, int i, int pi, const T* Z, int64_t ldz,
+                                       const Rot<T>* rot, ZItem<T>& it) {
+  round_pair(r, pi, kp, it.a, it.b);
+  if (it.a >= k || it.b >= k) return false;
+  const Rot<T> ra = rot[it.a], rb = rot[it.b];
+  it.as = ra.self;
+  it.ao = ra.other;
+  it.bs = rb.self;
+  it.bo = rb.other;
+  it.za = Z[i + (int64_t)it.a * ldz];
+  it.zb = Z[i + (int64_t)it.b * ldz];
+  return true;
+}
+
+template <typename T> __device__ __forceinline__ void z_store(int i, T* Z, int64_t ldz, const ZItem<T>& it) {
+  using s = S<T>;
+  Z[i + (int64_t)it.a * ldz] = s::add(s::mul(it.za, it.as), s::mul(it.zb, it.ao));
+  Z[i + (int64_t)it.b * ldz] = s::add(s::mul(it.zb, it.bs), s::mul(it.za, it.bo));
+}
+
 template <typename T>
 __device__ __forceinline__ void jacobi_apply_z(int k, int kp, int r, int i, int pi, T* Z, int64_t ldz,
                                                const Rot<T>* rot) {
-  using s = S<T>;
-  int a, b;
-  round_pair(r, pi, kp, a, b);
-  if (a >= k || b >= k) return;
-  Rot<T> ra = rot[a], rb = rot[b];
-  T za = Z[i + (int64_t)a * ldz], zb = Z[i + (int64_t)b * ldz];
-  Z[i + (int64_t)a * ldz] = s::add(s::mul(za, ra.self), s::mul(zb, ra.other));
-  Z[i + (int64_t)b * ldz] = s::add(s::mul(zb, rb.self), s::mul(za, rb.other));
+  ZItem<T> it;
+  if (z_load<T>(k, kp, r, i, pi, Z, ldz, rot, it)) z_store<T>(i, Z, ldz, it);
 }
 
 template <typename T>
@@ -162,6 +199,10 @@ __global__ void jacobi_apply_z_kernel(int k, int kp, int r, T* Z, int64_t ldz, c
 // launch).  Every barrier wait is bounded by a wall-clock limit; on expiry, or when another block
 // has flagged an error, the block sets/keeps the error flag and returns.
 constexpr unsigned long long GRID_WAIT_NS = 2000000000ull;
+constexpr int SWEEP_THREADS = 256;  // up to four blocks per SM (measured faster than one 1024-thread block)
+// barrier words, each in its own 32-byte sector so that the pollers of the generation word do not
+// contend with the arrival atomics
+constexpr int BAR_COUNT = 0, BAR_GEN = 8, BAR_ERR = 16, BAR_WORDS = 17;
 
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
@@ -169,33 +210,33 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-// bar[0]: arrivals, bar[1]: generation, bar[2]: error flag (all zero at launch)
+// bar[BAR_COUNT]: arrivals, bar[BAR_GEN]: generation, bar[BAR_ERR]: error flag (all zero at launch)
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
   __shared__ int ok_sh;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vb = bar;
-    int ok = vb[2] == 0u;
+    int ok = vb[BAR_ERR] == 0u;
     if (ok) {
-      const unsigned gen = vb[1];
+      const unsigned gen = vb[BAR_GEN];
       __threadfence();
-      if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
-        atomicExch(&bar[0], 0u);
+      if (atomicAdd(&bar[BAR_COUNT], 1u) == nblocks - 1) {
+        atomicExch(&bar[BAR_COUNT], 0u);
         __threadfence();
-        atomicAdd(&bar[1], 1u);
+        atomicAdd(&bar[BAR_GEN], 1u);
       } else {
         const unsigned long long t0 = gtimer();
-        while (vb[1] == gen) {
-          if (vb[2] != 0u) {
+        while (vb[BAR_GEN] == gen) {
+          if (vb[BAR_ERR] != 0u) {
             ok = 0;
             break;
           }
           if (gtimer() - t0 > GRID_WAIT_NS) {
-            atomicOr(&bar[2], 1u);
+            atomicOr(&bar[BAR_ERR], 1u);
             ok = 0;
             break;
           }
-          __nanosleep(64);
+          __nanosleep(100);
         }
       }
       __threadfence();
@@ -207,8 +248,8 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) jacobi_sweep_kernel(int k, int kp, T* G, int64_t ldg, T* Z, int64_t ldz,
-                                                           Rot<T>* rot, unsigned* bar) {
+__global__ void __launch_bounds__(SWEEP_THREADS, 4) jacobi_sweep_kernel(int k, int kp, T* G, int64_t ldg, T* Z,
+                                                                        int64_t ldz, Rot<T>* rot, unsigned* bar) {
   const int half = kp / 2;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
@@ -222,14 +263,15 @@ __global__ void __launch_bounds__(256) jacobi_sweep_kernel(int k, int kp, T* G, 
   }
 }
 
-// blocks of 256 threads that can be co-resident for the sweep kernel (0: no cooperative launch)
+// co-resident blocks of SWEEP_THREADS threads for the sweep kernel (0: no cooperative launch)
 template <typename T> static int sweep_grid() {
   static const int nb = []() {
     int dev = 0, sms = 0, per = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_sweep_kernel<T>, 256, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, jacobi_sweep_kernel<T>, SWEEP_THREADS, 0) != cudaSuccess)
+      return 0;
     return sms * std::min(per, 4);
   }();
   return nb;
@@ -314,9 +356,15 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
   double hstat[2];
   int sweeps = 0;
   bool done = false;
-  // one cooperative launch per sweep; the barrier words live in iwork (overwritten by the final
-  // ranking only after the sweeps)
-  const int coop_grid = (persistent && k >= 64) ? sweep_grid<T>() : 0;
+  // one cooperative launch per sweep; the barrier words live in iwork[0, BAR_WORDS) (k >= 64 ints;
+  // overwritten by the final ranking only after the sweeps)
+  // grid sized by the work of a round (about 4 rotation updates per thread), at most the co-resident
+  // maximum: small quotients take few SMs, which leaves room for other streams' kernels
+  int coop_grid = (persistent && k >= 64) ? sweep_grid<T>() : 0;
+  if (coop_grid > 0) {
+    const int64_t items = (int64_t)(kp / 2) * (kp / 2) + (int64_t)k * (kp / 2);
+    coop_grid = (int)std::max<int64_t>(1, std::min<int64_t>(coop_grid, ceil_div(items, 4 * SWEEP_THREADS)));
+  }
   unsigned* bar = reinterpret_cast<unsigned*>(iwork);
   unsigned bar_err = 0;
   for (; sweeps <= max_sweeps; ++sweeps) {
@@ -325,7 +373,8 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
     offdiag_sum_kernel<<<1, 32, 0, st>>>(k, part, dwork);
     CHASE_CHECK_LAUNCH();
     CHASE_CUDA(cudaMemcpyAsync(hstat, dwork, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (coop_grid > 0 && sweeps > 0) CHASE_CUDA(cudaMemcpyAsync(&bar_err, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    if (coop_grid > 0 && sweeps > 0)
+      CHASE_CUDA(cudaMemcpyAsync(&bar_err, bar + BAR_ERR, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CHASE_CUDA(cudaStreamSynchronize(st));
     CHASE_REQUIRE(bar_err == 0, 8, "heev_jacobi: a grid barrier of the sweep kernel hit its wait limit");
     CHASE_REQUIRE(isfinite(hstat[0]) && isfinite(hstat[1]), 5, "heev_jacobi: non-finite matrix");
@@ -338,14 +387,15 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
     dim3 gblk(16, 16), ggrid(ceil_div(half, 16), ceil_div(half, 16));
     dim3 zgrid(ceil_div(k, 128), half);
     if (coop_grid > 0) {
-      CHASE_CUDA(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
+      CHASE_CUDA(cudaMemsetAsync(bar, 0, BAR_WORDS * sizeof(unsigned), st));
       int kk = k, kpp = kp;
       int64_t ldgg = ldg, ldzz = k;
       T* Gp = G;
       T* Zp = Zu;
       Rot<T>* rp = rot;
       void* args[] = {&kk, &kpp, &Gp, &ldgg, &Zp, &ldzz, &rp, &bar};
-      CHASE_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel<T>, dim3(coop_grid), dim3(256), args, 0, st));
+      CHASE_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel<T>, dim3(coop_grid), dim3(SWEEP_THREADS),
+                                             args, 0, st));
       CHASE_CHECK_LAUNCH();
     } else {
       for (int r = 0; r < kp - 1; ++r) {

@@ -214,3 +214,23 @@ def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx, k):
     st = s.stats()
     assert st["rr_fallbacks"] == 0
     assert st["rr_clusters"] >= 1
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_solve_host_buffers_match_device(pkg, pinned):
+    """chase_solve given host A, V0, L0 (pinned or pageable) copies them itself and returns the same
+    eigenpairs as the device-pointer call."""
+    import torch
+    p = G.problem_c1()
+    A = p.dense()
+    s = pkg.Chase(p.n, p.ne, complex_=True)
+    w_d, V_d = s.solve(dev(A), p.nev, p.nex, p.tol, p.deg, "fp64", dev(p.V0), dev(p.L0))
+    hostT = lambda x: torch.from_numpy(np.ascontiguousarray(np.asarray(x).T))
+    Ah, V0h, L0h = hostT(A), hostT(p.V0), hostT(p.L0)
+    if pinned:
+        Ah, V0h, L0h = Ah.pin_memory(), V0h.pin_memory(), L0h.pin_memory()
+    w_h, V_h = s.solve(Ah, p.nev, p.nex, p.tol, p.deg, "fp64", V0h, L0h)
+    assert not w_h.is_cuda and not V_h.is_cuda
+    assert np.array_equal(w_h.numpy(), w_d.cpu().numpy())
+    assert np.array_equal(V_h.numpy(), V_d.cpu().numpy())
+    assert np.max(np.abs(w_h.numpy() - p.lam[:p.nev])) <= 1e-10 * p.norm2()
