@@ -68,6 +68,29 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_over_ranks(values, op="max", device=None):
+    """Element-wise max or sum of a list of numbers over all ranks of the default process group
+    (the identity without one).  device: where the reduction tensor lives (a CUDA device for NCCL,
+    None for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t.tolist()]
+
+
+def shard(items, ws, rank):
+    """Rank's share of independent work items (round robin): disjoint across ranks, covering all."""
+    return list(items)[rank::ws]
+
+
+def whole_job_tflops(flops_all_ranks, ms_slowest):
+    """Whole-job throughput: the work of all ranks over the slowest rank's time."""
+    return flops_all_ranks / (ms_slowest * 1e-3) / 1e12
+
+
 def problem(args):
     from gen import problems as G
     n_low = int(round(2000 * args.n / 30000))
@@ -244,7 +267,7 @@ def backward_timing(pkg, np, torch, dev, n=16384, nev=64, nex=32):
     return out
 
 
-def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4):
+def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4, ws=1, rank=0):
     """The batched warm-start workload: 64 complex Hermitian problems, n uniform in [512, 8192],
     lam U[-1,1], 8 reflectors, nev = 5% of n, nex = nev/2, each a 4-step sequence
     A_{k+1} = A_k + 1e-3 H_k restarted from the previous eigenvectors.
@@ -254,7 +277,8 @@ def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4):
     solved with one worker (problems one after the other) for comparison.
     """
     from gen import problems as G
-    probs = [G.problem_c4(pid) for pid in range(nprob)]
+    pids = shard(range(nprob), ws, rank)  # replicas: each rank solves its own problems, no exchange
+    probs = [G.problem_c4(pid) for pid in pids]
     tdev = lambda x: torch.from_numpy(np.ascontiguousarray(np.asarray(x).T)).to(dev)
     n_max = max(p.n for p in probs)
     ne_max = max(p.ne for p in probs)
@@ -303,9 +327,11 @@ def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4):
                                                         zip(ws, probs)))
         per_step.append(rec)
         for q, p in enumerate(probs):
-            ctx.perturb(A[q], 1e-3, G.sequence_seed(q, step))
+            ctx.perturb(A[q], 1e-3, G.sequence_seed(pids[q], step))
     ctx.close()
-    out.update({"per_step": per_step, "total_s": t_total, "filter_tflops_wall": flops / t_total / 1e12,
+    t_total, = reduce_over_ranks([t_total], "max", dev)
+    flops, = reduce_over_ranks([flops], "sum", dev)
+    out.update({"per_step": per_step, "total_s": t_total, "filter_tflops_wall": whole_job_tflops(flops, 1e3 * t_total),
                 "speedup_step0_vs_one_worker": out["step0_one_worker_s"] / per_step[0]["seconds"]})
     del A, V, V0, L0
     torch.cuda.empty_cache()
@@ -370,15 +396,12 @@ def run_ours(args):
     clk = clocks.stop()
     launches = pkg.kernel_launch_count() - launches0
     t_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
     flops = sum(8.0 * n * n * s["matvecs"] for s in stats)
     filter_ms = sum(s["ms_filter"] for s in stats)
     # whole-job filter throughput: all ranks' filter flops over the slowest rank's filter time
-    value = ws * flops / (filter_ms * 1e-3) / 1e12
+    t_ms, filter_ms = reduce_over_ranks([t_ms, filter_ms], "max", dev)
+    (flops_all,) = reduce_over_ranks([flops], "sum", dev)
+    value = whole_job_tflops(flops_all, filter_ms)
     ms_step = t_ms / args.steps
 
     # roofline of the dominant kernel: the FP64-class split-product GEMM of the filter
@@ -474,7 +497,7 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         try:
-            batched = batched_timing(pkg, np, torch, dev, args.batch_workers)
+            batched = batched_timing(pkg, np, torch, dev, args.batch_workers, ws=ws, rank=rank)
         except Exception as ex:
             batched = {"error": repr(ex)[:300]}
 
