@@ -413,8 +413,14 @@ def run_ours(args):
     split_flops = sum(8.0 * pairs * n * n * s["matvecs"] for s in stats)
     achieved = split_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
     peak = pk.get("bf16_tflops_sustained")
+    # DRAM traffic of one filter launch at this size (n = 30000, 1600 columns), from a one-pass ncu capture of
+    # `bench.py --hemm-only fp64` (dram__bytes_read.sum 713.09 GB + dram__bytes_write.sum 13.02 GB); it
+    # describes the kernel as built now and must be re-captured (or set to None) when the kernel changes
+    traffic = 726.11e9 if (n, ne, slices) == (30000, 1600, 7) else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": None,
+                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "algorithmic_bytes_per_launch": 2.0 * 2 * slices * n * n + 2.0 * 3 * slices * ne * n + 3 * 16.0 * n * ne,
                 "kernel": f"oz_gemm_kernel<S={slices},exact levels=5,complex> (bf16 split products, "
                           f"{pairs} digit pairs per complex product)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
