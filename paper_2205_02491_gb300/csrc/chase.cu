@@ -1051,7 +1051,10 @@ chase_status chase_solve(chase_ctx* c, const void* A, int64_t n, int64_t lda, in
       CHASE_CUDA(cudaMalloc(&c->a_stage, need));
       c->a_stage_bytes = need;
     }
-    CHASE_CUDA(cudaMemcpy2DAsync(c->a_stage, n * esz, A, lda * esz, n * esz, n, cudaMemcpyHostToDevice, c->stream));
+    if (lda == n)
+      CHASE_CUDA(cudaMemcpyAsync(c->a_stage, A, need, cudaMemcpyHostToDevice, c->stream));
+    else
+      CHASE_CUDA(cudaMemcpy2DAsync(c->a_stage, n * esz, A, lda * esz, n * esz, n, cudaMemcpyHostToDevice, c->stream));
     A = c->a_stage;
     lda = n;
   }

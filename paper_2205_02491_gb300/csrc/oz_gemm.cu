@@ -159,6 +159,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
+// Same MMA with a collector-buffer hint for A: COL 1 fill (read A, keep it), 2 use (A from the collector),
+// 3 lastuse (A from the collector, then released); 0 none.  Consecutive MMAs that share one A tile read it
+// from shared memory once.
+template <int COL>
+__device__ __forceinline__ void mma_bf16_c(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t acc) {
+  if (COL == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  else if (COL == 2)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  else if (COL == 3)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  else
+    mma_bf16(tmem_d, adesc, bdesc, idesc, acc);
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -331,28 +356,37 @@ __global__ void __maxnreg__(168)
     int a_iter = 0;
     bool ok = true;
     // MMAs of slice t (all its pairs in `pass`: 0 all, 1 inexact levels, 2 exact levels), both K-steps.
-    // t and u are compile-time after unrolling, so level, accumulator and descriptor offsets fold.
+    // Per A plane and K-step, the MMAs over the right-operand slices u run back to back and share one A
+    // tile through the collector buffer (fill, use..., lastuse).  t and u are compile-time after
+    // unrolling, so levels, accumulators, descriptor offsets and collector hints fold.
     auto issue_slice = [&](const int t, const int pass, const uint64_t adesc, const uint64_t bdesc) {
+      int ulo = 0, uhi = Cf::MAXLEVEL - t;  // u range: levels t + ulo .. t + uhi
+      if (pass == 1) ulo = NEX - t > 0 ? NEX - t : 0;
+      if (pass == 2 && NEX - 1 - t < uhi) uhi = NEX - 1 - t;
+      if (uhi < ulo) return;
+      const int cnt = uhi - ulo + 1;
 #pragma unroll
-      for (int u = S - 1; u >= 0; --u) {
-        if (u > Cf::MAXLEVEL - t) continue;
-        const int level = t + u;
-        if (pass == 1 && level < NEX) continue;
-        if (pass == 2 && level >= NEX) continue;
-        const int acc = level < NEX ? level : NEX;
-        const uint32_t dt = tmem + (uint32_t)(acc * Cf::NT);
-        const uint64_t bslice = bdesc + (uint64_t)((u * Cf::B_SLICE) >> 4);
+      for (int pl = 0; pl < Cf::AP; ++pl) {
 #pragma unroll
         for (int ks = 0; ks < BK / 16; ++ks) {
           const uint64_t ko = (uint64_t)(ks * 2);  // 32 bytes along K, in 16-byte units
-          const uint32_t en = ((fresh >> acc) & 1u) ? 0u : 1u;
-          fresh &= ~(1u << acc);
-          if (CPLX) {
-            // [Cr | Ci] += Ar [Yr | Yi] + Ai [-Yi | Yr]
-            mma_bf16(dt, adesc + ko, bslice + (uint64_t)(Cf::B_PLANE >> 4) + ko, IDESC, en);
-            mma_bf16(dt, adesc + (uint64_t)(Cf::A_PLANE >> 4) + ko, bslice + ko, IDESC, 1u);
-          } else {
-            mma_bf16(dt, adesc + ko, bslice + ko, IDESC, en);
+          const uint64_t a = adesc + (uint64_t)((pl * Cf::A_PLANE) >> 4) + ko;
+#pragma unroll
+          for (int i = 0; i < S; ++i) {
+            if (i >= cnt) continue;
+            const int u = uhi - i;
+            const int level = t + u;
+            const int acc = level < NEX ? level : NEX;
+            const uint32_t dt = tmem + (uint32_t)(acc * Cf::NT);
+            const uint64_t bslice = bdesc + (uint64_t)((u * Cf::B_SLICE) >> 4);
+            // complex: [Cr | Ci] += Ar [Yr | Yi] (planes 1, 2) + Ai [-Yi | Yr] (planes 0, 1)
+            const uint64_t b = (CPLX && pl == 0 ? bslice + (uint64_t)(Cf::B_PLANE >> 4) : bslice) + ko;
+            const uint32_t en = ((fresh >> acc) & 1u) ? 0u : 1u;
+            fresh &= ~(1u << acc);
+            if (cnt == 1) mma_bf16_c<0>(dt, a, b, IDESC, en);
+            else if (i == 0) mma_bf16_c<1>(dt, a, b, IDESC, en);
+            else if (i == cnt - 1) mma_bf16_c<3>(dt, a, b, IDESC, en);
+            else mma_bf16_c<2>(dt, a, b, IDESC, en);
           }
         }
       }
