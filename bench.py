@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--table2", action="store_true",
                     help="instead of the default run: the eigen-type suite of Table 2 (real symmetric n = 20000: "
                          "1-2-1, Wilkinson, Uniform, Geometric; nev 1500, nex 500), one FP64 solve each")
+    ap.add_argument("--types", default="1-2-1,Wilkinson,Uniform,Geometric", help="--table2: matrix types to run")
+    ap.add_argument("--maxiter", type=int, default=30, help="--table2: outer-iteration cap")
     ap.add_argument("--mixed-large", action="store_true",
                     help="instead of the default run: time-to-solution of the n = 60000 mixed-precision workload "
                          "in FP64 and in each mixed mode (one JSON line; about ten minutes)")
@@ -635,9 +637,11 @@ def run_table2(args):
     n, nev, nex = 20000, 1500, 500
     ne = nev + nex
     tdev = lambda x: torch.from_numpy(np.ascontiguousarray(np.asarray(x).T)).to(dev)
-    ctx = pkg.Chase(n, ne, complex_=False)
+    ctx = pkg.Chase(n, ne, complex_=False, opts={"maxiter": args.maxiter})
     out = {}
     for pid, name in enumerate(("1-2-1", "Wilkinson", "Uniform", "Geometric")):
+        if name not in args.types.split(","):
+            continue
         At = torch.zeros((n, n), dtype=torch.float64, device=dev)
         exact = None
         if name in ("1-2-1", "Wilkinson"):
@@ -673,7 +677,8 @@ def run_table2(args):
         print(json.dumps({name: out[name]}), file=sys.stderr, flush=True)
         del At, V0t, L0t
     ctx.close()
-    print(json.dumps({"table2": {"n": n, "nev": nev, "nex": nex, "dtype": "real symmetric f64, FP64-class products",
+    print(json.dumps({"table2": {"n": n, "nev": nev, "nex": nex, "maxiter": args.maxiter,
+                                 "dtype": "real symmetric f64, FP64-class products",
                                  "types": out}}), flush=True)
     return 0
 
