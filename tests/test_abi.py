@@ -62,3 +62,33 @@ def test_create_rejects_bad_arguments_without_gpu_work(lib):
     assert lib.chase_create(C.byref(ctx), 10, 20, _lib.CHASE_C128, None, None) == 1
     assert lib.chase_create(C.byref(ctx), 10, 5, 7, None, None) == 1
     assert lib.chase_solve(None, None, 1, 1, 1, 0, 1e-10, 1, 0, None, None) == 1
+
+
+def _header_struct_fields(name):
+    """(type, field) pairs of `typedef struct { ... } name;` in include/chase_gb300.h, in order."""
+    txt = open(os.path.join(ROOT, "include", "chase_gb300.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", txt)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, rest = decl.split(None, 1)
+        for f in rest.split(","):
+            fields.append((typ, f.strip()))
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("chase_opts", "Opts"), ("chase_stats_t", "Stats")])
+def test_ctypes_structs_mirror_the_header(cname, pyname):
+    """The ctypes mirrors of the option and statistics structs have the header's fields, types and order
+    (a mismatch would silently shift every field after it)."""
+    import ctypes as C
+    from paper_2205_02491_gb300 import _lib
+    ctype = {"int": C.c_int, "int64_t": C.c_int64, "double": C.c_double}
+    hdr = _header_struct_fields(cname)
+    py = getattr(_lib, pyname)._fields_
+    assert [f for _, f in hdr] == [f for f, _ in py]
+    assert [ctype[t] for t, _ in hdr] == [t for _, t in py]
