@@ -287,6 +287,30 @@ def test_solve_121_closed_form():
     assert np.max(np.abs(r.eigvals - G.spectrum_121(n)[:8])) <= 1e-10 * 4
 
 
+def test_warm_start_from_previous_eigenvectors_needs_fewer_matvecs():
+    """Correlated sequence (the premise of the batched form): after A -> A + 1e-3 H, restarting from the
+    previous eigenvectors (padded with the rest of the previous search block) converges to the new
+    spectrum with fewer filter products than a cold start from the random block."""
+    n, nev, nex = 300, 12, 8
+    p = G.problem_c4(3, n)
+    p = G.from_dense("seq", p.dense(), nev, nex)
+    A0 = p.dense()
+    r0 = O.chase_solve(A0, nev, nex, 1e-10, 20, 36, p.V0, p.L0, 25)
+    assert r0.converged
+    A1 = A0 + 1e-3 * G.perturbation(n, G.sequence_seed(3, 0), True)
+    # warm block: the locked eigenvectors, then the remaining random columns re-orthogonalised against them
+    rest = p.V0[:, nev:] - r0.eigvecs @ (np.conj(r0.eigvecs.T) @ p.V0[:, nev:])
+    V_warm = np.concatenate([r0.eigvecs, rest], axis=1)
+    cold = O.chase_solve(A1, nev, nex, 1e-10, 20, 36, p.V0, p.L0, 25)
+    warm = O.chase_solve(A1, nev, nex, 1e-10, 20, 36, V_warm, p.L0, 25)
+    ref = np.linalg.eigvalsh(A1)[:nev]
+    nrm = np.max(np.abs(np.linalg.eigvalsh(A1)))
+    for r in (cold, warm):
+        assert r.converged
+        assert np.max(np.abs(r.eigvals - ref)) <= 1e-10 * nrm
+    assert warm.matvecs < cold.matvecs
+
+
 def test_planted_sign_error_in_filter_is_caught(monkeypatch):
     # a plausible mistake (wrong sign of the three-term beta) must fail the closed-form pin
     orig = O.filter_coefficients
