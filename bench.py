@@ -443,10 +443,14 @@ def run_ours(args):
         # every rank on this node pins a host copy of A: skip (and say so) when the host lacks the memory
         local_ws = int(os.environ.get("LOCAL_WORLD_SIZE", "1"))
         need = 1.25 * 16 * n * (n + ne + 8) * local_ws
+        avail = None
         try:
-            avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
-        except (ValueError, OSError):
-            avail = None
+            with open("/proc/meminfo") as f:
+                for line in f:
+                    if line.startswith("MemAvailable:"):
+                        avail = int(line.split()[1]) * 1024
+        except OSError:
+            pass
         if avail is not None and avail < need:
             raise RuntimeError(f"skipped: {local_ws} rank(s) would pin {need / 1e9:.0f} GB of host memory, "
                                f"{avail / 1e9:.0f} GB available")
