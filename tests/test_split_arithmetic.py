@@ -10,7 +10,8 @@ The claims checked here:
 - the exact levels 0..4 of one product add up to at most 2^14 (1 + 2^-29) in level-0 units, so their int64
   accumulation in units of 2^-32 cannot overflow for K <= 65472 (and that limit is tight);
 - the level-by-level product equals the FP64 product to 2^-49 per K term (the parity tests' bound) when levels
-  0..4 are exact and the rest are rounded.
+  0..4 are exact and the rest are rounded;
+- the mixed modes (2 or 3 slices, one rounded accumulator) meet the per-term bounds 2^-13 and 2^-20.
 """
 import numpy as np
 import pytest
@@ -149,3 +150,23 @@ def test_level_product_meets_the_fp64_parity_bound():
     ra = np.max(np.abs(A), axis=1)
     cb = np.max(np.abs(B), axis=0)
     assert np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / K <= 2.0 ** -49
+
+
+@pytest.mark.parametrize("S,bound", [(2, 2.0 ** -13), (3, 2.0 ** -20)])
+def test_mixed_mode_products_meet_their_bounds(S, bound):
+    """The mixed modes (2 or 3 slices, 3 or 6 digit pairs, one rounded FP32 accumulator) stay within the
+    per-term bounds the GPU tests use for them."""
+    g = np.random.default_rng(20 + S)
+    M, K, N = 16, 512, 12
+    A = g.standard_normal((M, K))
+    B = g.standard_normal((K, N))
+    C = _split_product(A, B, S, 0)
+    ref = (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
+    ra = np.max(np.abs(A), axis=1)
+    cb = np.max(np.abs(B), axis=0)
+    err = np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / K
+    assert err <= bound
+    # and the truncation is what limits them: one slice fewer would not meet the bound
+    C1 = _split_product(A, B, S - 1, 0) if S > 2 else None
+    if C1 is not None:
+        assert np.max(np.abs(C1 - ref) / (ra[:, None] * cb[None, :])) / K > bound
