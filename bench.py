@@ -334,9 +334,8 @@ def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4, ws=1, rank=0
         for q, p in enumerate(probs):
             ctx.perturb(A[q], 1e-3, G.sequence_seed(pids[q], step))
     ctx.close()
-    t_total, = reduce_over_ranks([t_total], "max", dev)
-    flops, = reduce_over_ranks([flops], "sum", dev)
-    out.update({"per_step": per_step, "total_s": t_total, "filter_tflops_wall": whole_job_tflops(flops, 1e3 * t_total),
+    # rank-local figures; the caller reduces the whole-job ones over ranks
+    out.update({"per_step": per_step, "total_s_rank": t_total, "filter_flops_rank": flops,
                 "speedup_step0_vs_one_worker": out["step0_one_worker_s"] / per_step[0]["seconds"]})
     del A, V, V0, L0
     torch.cuda.empty_cache()
@@ -526,6 +525,16 @@ def run_ours(args):
             batched = batched_timing(pkg, np, torch, dev, args.batch_workers, ws=ws, rank=rank)
         except Exception as ex:
             batched = {"error": repr(ex)[:300]}
+        # every rank takes part in the reductions, also after a local failure (no rank is left waiting)
+        ok = 0.0 if "error" in batched else 1.0
+        t_loc = batched.get("total_s_rank", 0.0)
+        f_loc = batched.get("filter_flops_rank", 0.0)
+        t_max, neg_min_ok = reduce_over_ranks([t_loc, -ok], "max", dev)  # max of -ok = -(min over ranks)
+        (f_sum,) = reduce_over_ranks([f_loc], "sum", dev)
+        if -neg_min_ok > 0.5 and t_max > 0:
+            batched.update({"total_s": t_max, "filter_tflops_wall": whole_job_tflops(f_sum, 1e3 * t_max)})
+        elif "error" not in batched:
+            batched["error"] = "another rank failed"
 
     cpu = None
     if rank == 0 and ws == 1:
