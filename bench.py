@@ -319,7 +319,7 @@ def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4, ws=1, rank=0
     for step in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ws, stats = ctx.solve_batched(A, nevs, nexs, 1e-10, 20, "fp64", V, L0)
+        wvals, stats = ctx.solve_batched(A, nevs, nexs, 1e-10, 20, "fp64", V, L0)
         dt = time.perf_counter() - t0
         t_total += dt
         fl = sum(8.0 * p.n * p.n * st["matvecs"] for p, st in zip(probs, stats))
@@ -329,7 +329,7 @@ def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4, ws=1, rank=0
                "max_resid": max(st["max_resid"] for st in stats), "filter_tflops_wall": fl / dt / 1e12}
         if step == 0:  # exact spectrum known before the first perturbation
             rec["max_abs_eig_err_vs_exact"] = float(max(np.max(np.abs(w.cpu().numpy() - p.lam[:p.nev])) for w, p in
-                                                        zip(ws, probs)))
+                                                        zip(wvals, probs)))
         per_step.append(rec)
         for q, p in enumerate(probs):
             ctx.perturb(A[q], 1e-3, G.sequence_seed(pids[q], step))
