@@ -647,8 +647,9 @@ def run_table2(args):
     tol 1e-10, degrees 20..36, one FP64-class solve per type with the per-stage split.
 
     1-2-1 and Wilkinson are the tridiagonal matrices (Wilkinson diagonal |i - (n-1)/2|); Uniform and
-    Geometric are Q diag(lam) Q^T with the Table 1 spectra (dmax 1, eps 1e-4) and Q a product of 16
-    seeded Householder reflectors (standing in for the paper's DEMAGIS matrices).  Eigenvalue error is
+    Geometric are Q diag(lam) Q^T with the Table 1 spectra (eps 1e-4; Uniform dmax = 1, Geometric
+    dmax = -1 so that its sparse end is the one computed) and Q a product of 16 seeded Householder
+    reflectors (standing in for the paper's DEMAGIS matrices).  Eigenvalue error is
     against the closed form (1-2-1) or the prescribed spectrum; Wilkinson reports the residual only.
     """
     import numpy as np
@@ -676,7 +677,7 @@ def run_table2(args):
             if name == "1-2-1":
                 exact = G.spectrum_121(n)[:nev]
         else:
-            lam = G.spectrum_uniform_table1(n) if name == "Uniform" else G.spectrum_geometric_table1(n)
+            lam = G.spectrum_uniform_table1(n) if name == "Uniform" else G.spectrum_geometric_table2(n)
             U = G.gaussian(G.rng(6, pid, 1), (n, 16), False)
             Bw, Dw = G.wy_factors(lam, U)
             ctx.generate(At, torch.from_numpy(lam).to(dev), tdev(U), tdev(Bw), tdev(Dw))

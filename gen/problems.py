@@ -57,6 +57,17 @@ def spectrum_geometric_table1(n: int, dmax: float = 1.0, eps: float = 1e-4) -> n
     return dmax * eps ** ((n - k) / (n - 1))
 
 
+def spectrum_geometric_table2(n: int, eps: float = 1e-4) -> np.ndarray:
+    """Geometric matrix of the eigen-type suite (Table 2), ascending: Table 1's formula with dmax = -1.
+
+    The eigenvalues lie in [-1, -eps] (condition number 1/eps = 1e4, as the paper prints) and follow a
+    geometric law, clustered toward zero and sparse at the lower end the solver computes.  With dmax = +1
+    the lowest eigenvalues are the clustered ones; the filter bound that rules that reading out is checked
+    in the tests.
+    """
+    return np.sort(spectrum_geometric_table1(n, dmax=-1.0, eps=eps))
+
+
 def spectrum_121(n: int) -> np.ndarray:
     """Table 1, (1-2-1): lambda_k = 2 - 2 cos(pi k / (n+1)), ascending."""
     k = np.arange(1, n + 1, dtype=np.float64)

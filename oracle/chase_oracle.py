@@ -10,13 +10,18 @@ paper: numpy FP64 arithmetic, a matmul as the only library primitive on the
 solver path, no blocking or fusion.  Where the paper is silent the reading used
 is stated in the docstring.
 
-Pins (see tests/test_oracle_*.py):
+Pins (tests/test_oracle.py):
   * Jacobi eigensolver: brute force vs LAPACK eigh, closed-form (1-2-1) spectrum,
     Sturm-bisection Wilkinson spectrum, orthonormality/residual invariants.
   * Householder QR: Q^H Q = I, Q R = X, span equality with LAPACK QR.
-  * Filter: exact scalar Chebyshev polynomial on eigenvectors (closed form).
-  * Lanczos: b_sup >= lambda_max and mu_1 >= lambda_min on prescribed spectra.
-  * Full solve: prescribed spectra and exact eigenvectors Q e_i.
+  * Filter: exact scalar Chebyshev polynomial on eigenvectors (closed form); the
+    row-block step against the same rows of the full filter.
+  * Lanczos: b_sup >= lambda_max and mu_1 >= lambda_min on prescribed spectra; the
+    DoS quantile mu_ne equals the quantile of the spectral measure computed from
+    eigh when the runs take n steps, and lies within one Ritz spacing of lambda_ne
+    with 25 steps.
+  * Full solve: prescribed spectra and exact eigenvectors Q e_i; the Table 2
+    Geometric type at a tenth of its size.
   * Degrees: parity unpinned (the paper gives no formula; affects only Matvecs).
   * Backward: dense full-eigendecomposition gradient and central finite differences.
 """

@@ -207,6 +207,126 @@ def test_lanczos_tridiagonal_exact_on_small_matrix():
     assert np.max(np.abs(lz.thetas[0] - p.lam)) <= 1e-12
 
 
+
+def _dos_quantile_from_eigh(A, starts, ne):
+    """The density-of-states quantile written from a full eigendecomposition (LAPACK eigh).
+
+    The spectral measure of a unit start vector v puts weight |q_j^H v|^2 on eigenvalue lambda_j; the
+    quantile is the smallest lambda_j at which the run-averaged measure reaches ne/n.
+    """
+    lam, Q = np.linalg.eigh(A)
+    n = A.shape[0]
+    wts = np.zeros(n)
+    for r in range(starts.shape[1]):
+        v = starts[:, r] / np.linalg.norm(starts[:, r])
+        wts += np.abs(np.conj(Q.T) @ v) ** 2 / starts.shape[1]
+    cdf = np.cumsum(wts)
+    j = int(np.argmax(cdf >= ne / n))
+    return lam, cdf, j
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_lanczos_dos_quantile_exact_with_full_steps(cplx):
+    """With n Lanczos steps each run's Ritz values are the eigenvalues of A and tau_j^2 = |q_j^H v|^2
+    (Gauss quadrature of the spectral measure is then exact), so the DoS estimate of mu_ne must equal
+    the quantile computed from eigh alone.  A wrong weighting (last instead of first components, no
+    1/runs) or an off-by-one in the quantile picks another eigenvalue and fails."""
+    n = 40
+    lam_p = np.linspace(-1.0, 1.0, n) + 0.3 * np.sin(np.arange(n))  # distinct, irregular gaps
+    lam_p = np.sort(lam_p)
+    p = G.problem_small(n, 4, 3, complex_=cplx, lam=lam_p, seed_pid=11)
+    A = p.dense()
+    for ne in (3, 7, 11):
+        lz = O.lanczos_bounds(A, p.L0, n, ne)
+        lam, cdf, j = _dos_quantile_from_eigh(A, p.L0, ne)
+        # the crossing is not at a rounding-level tie
+        assert cdf[j] - ne / n > 1e-6 and (j == 0 or ne / n - cdf[j - 1] > 1e-6)
+        span = lz.b_sup - lz.mu_1
+        assert abs(lz.b_sup - lam[-1]) <= 1e-10 and abs(lz.mu_1 - lam[0]) <= 1e-10
+        expect = min(max(lam[j], lz.mu_1 + 1e-3 * span), lz.b_sup - 1e-3 * span)
+        assert abs(lz.mu_ne - expect) <= 1e-10 * span, (ne, lz.mu_ne, expect)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_lanczos_dos_quantile_statistical(cplx):
+    """With the reading's 4 runs of 25 steps the DoS estimate is a quadrature of the spectral measure, so
+    the index of mu_ne in the spectrum lies within about one Ritz spacing (n/steps eigenvalues) of ne in
+    every seeded case and is unbiased on average."""
+    n, steps = 300, 25
+    for ne in (16, 30, 60):
+        idx = []
+        for pid in range(8):
+            p = G.problem_small(n, ne // 2, ne - ne // 2, complex_=cplx, seed_pid=pid)
+            lz = O.lanczos_bounds(p.dense(), p.L0, steps, ne)
+            idx.append(int(np.sum(p.lam <= lz.mu_ne)))
+        assert max(abs(i - ne) for i in idx) <= n // steps, (ne, idx)
+        assert abs(np.mean(idx) - ne) <= 0.15 * ne + 1, (ne, idx)
+
+
+def test_chebyshev_step_rows_matches_filter():
+    """The row-block step (the CPU sample the benchmark times) equals the same rows of the full filter."""
+    p = G.problem_small(90, 6, 4, complex_=True, seed_pid=5)
+    A = p.dense()
+    V = p.V0
+    b_sup, mu_1, mu_ne = 1.05, -1.0, -0.4
+    c, e, al, be = O.filter_coefficients(b_sup, mu_1, mu_ne, 6)
+    rows = np.arange(17, 53)
+    for s in (1, 2, 5, 6):
+        Ys = O.chebyshev_filter(A, V, np.full(V.shape[1], s), b_sup, mu_1, mu_ne)[0]
+        Y1 = O.chebyshev_filter(A, V, np.full(V.shape[1], s - 1), b_sup, mu_1, mu_ne)[0] if s > 1 else V
+        Y2 = O.chebyshev_filter(A, V, np.full(V.shape[1], s - 2), b_sup, mu_1, mu_ne)[0] if s > 2 else V
+        out = O.chebyshev_step_rows(A[rows], rows, Y1, Y2[rows], s, c, al, be)
+        assert np.max(np.abs(out - Ys[rows])) <= 1e-12 * max(1.0, np.max(np.abs(Ys))), s
+
+
+# ---------------------------------------------------------------- Table 2 Geometric reading
+
+def _cheb_growth(t, m):
+    return np.cosh(m * np.arccosh(abs(t)))
+
+
+def test_table2_geometric_positive_dmax_contradicts_paper_counts():
+    """Table 2 solves the Geometric matrix (n = 20k, nev 1500, nex 500) in 8 iterations with 285192
+    Matvecs.  With Table 1's formula and dmax = +1 the 2000 lowest eigenvalues fall in [1e-4, 2.5e-4]
+    of a spectrum of norm 1.  A polynomial of degree m bounded by 1 on the unwanted interval
+    [lambda_{ne+1}, lambda_n] is at most C_m(|t|) at lambda_nev (Chebyshev's minimax property); with
+    degrees <= 36, 8 iterations apply at most degree 20 + 7 * 36 = 272, which separates lambda_nev from
+    the unwanted part by a factor below 100, while a residual of 1e-10 needs about 1e9.  The degree
+    formula also returns the cap for every wanted vector there, whereas the paper's Matvecs average
+    17.8 per vector and iteration.  With dmax = -1 (the reading used for Table 2) the lowest
+    eigenvalues are the sparse end and one degree-20 filter already separates them by more than 1e6."""
+    n, nev, ne = 20000, 1500, 2000
+    for lam, converges in ((G.spectrum_geometric_table1(n), False), (G.spectrum_geometric_table2(n), True)):
+        a, b = lam[ne], lam[-1]                 # unwanted interval [lambda_{ne+1}, lambda_n]
+        c, e = 0.5 * (a + b), 0.5 * (b - a)
+        t = (lam[nev - 1] - c) / e
+        assert abs(t) > 1
+        if converges:
+            assert _cheb_growth(t, 20) > 1e6
+        else:
+            assert _cheb_growth(t, 20 + 7 * 36) < 100
+            rho = abs(t) + np.sqrt(t * t - 1)
+            assert np.log(10.0) / np.log(rho) > 36   # one decade of residual needs more than the cap
+    # both readings have the condition number the paper prints
+    for lam in (G.spectrum_geometric_table1(n), G.spectrum_geometric_table2(n)):
+        assert abs(np.max(np.abs(lam)) / np.min(np.abs(lam)) - 1e4) <= 1e-6 * 1e4
+    assert 285192 / (ne * 8) < 18
+
+
+def test_solve_table2_geometric_scaled():
+    """The Table 2 Geometric type at a tenth of the size (n = 2000, nev 150, nex 50, the same
+    spectral shape) converges in the oracle to the prescribed eigenvalues."""
+    n, nev, nex = 2000, 150, 50
+    lam = G.spectrum_geometric_table2(n)
+    p = G.problem_small(n, nev, nex, complex_=False, k_reflect=8, lam=lam, seed_pid=7)
+    A = p.dense()
+    r = O.chase_solve(A, nev, nex, 1e-10, 20, 36, p.V0, p.L0, 25)
+    assert r.converged and r.iterations <= 8
+    assert np.max(np.abs(r.eigvals - lam[:nev])) <= 1e-10
+    R = A @ r.eigvecs - r.eigvecs * r.eigvals[None, :]
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * 1.0000001
+
+
 # ---------------------------------------------------------------- residuals, degrees, locking
 
 def test_residuals_and_lock():
