@@ -156,6 +156,19 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one full-width filter launch of the
+# current kernel, captured at n = 8192 with 1600 columns (one launch, --clock-control none) and scaled to
+# the bench's n by (n / 8192)^2: the A planes are read once per launch and the right-operand planes once
+# per row block of tiles, both proportional to n^2 at a fixed column count.  None until captured.
+FILTER_TRAFFIC_N8192 = None
+
+
+def filter_traffic_bytes(n, ne, slices):
+    if FILTER_TRAFFIC_N8192 is None or ne != 1600 or slices != 7:
+        return None
+    return FILTER_TRAFFIC_N8192 * (n / 8192.0) ** 2
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -408,28 +421,41 @@ def run_ours(args):
     value = whole_job_tflops(flops_all, filter_ms)
     ms_step = t_ms / args.steps
 
-    # roofline of the dominant kernel: the FP64-class split-product GEMM of the filter
+    # roofline of the dominant kernel: the FP64-class split-product GEMM of the filter.  Work is the
+    # algorithmic HEMM work of the launches (8 n^2 flops per column and degree step, complex), over the
+    # CUDA-event time of those launches, against the bf16 tensor peak the kernel runs on; the split
+    # products' own bf16 work (digit pairs x the algorithmic work) is reported beside it as the
+    # emulation's efficiency.
     pk = peaks()
     slices = int(one.opts.oz_slices)
     pairs = slices * (slices + 1) // 2
     kern_ms = sum(s["ms_filter_kernel"] for s in stats)
     kern_launches = sum(s["filter_kernel_launches"] for s in stats)
-    split_flops = sum(8.0 * pairs * n * n * s["matvecs"] for s in stats)
-    achieved = split_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
+    alg_flops = sum(8.0 * n * n * s["matvecs"] for s in stats)
+    split_flops = pairs * alg_flops
+    achieved = alg_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
+    split_tflops = split_flops / (kern_ms * 1e-3) / 1e12 if kern_ms > 0 else None
     peak = pk.get("bf16_tflops_sustained")
-    # DRAM traffic of one filter launch at this size (n = 30000, 1600 columns), from a one-pass ncu capture of
-    # `bench.py --hemm-only fp64` (dram__bytes_read.sum 728.02 GB + dram__bytes_write.sum 14.15 GB); it
-    # describes the kernel as built now and must be re-captured (or set to None) when the kernel changes
-    traffic = 742.17e9 if (n, ne, slices) == (30000, 1600, 7) else None
+    try:
+        fp64_units = {"dfma_tflops": pkg.measure_fp64_peak("dfma"), "dmma_tflops": pkg.measure_fp64_peak("dmma")}
+        fp64_units["filter_over_best_fp64_unit"] = (achieved / max(fp64_units["dfma_tflops"], fp64_units["dmma_tflops"])
+                                                    if achieved else None)
+    except Exception as ex:
+        fp64_units = {"error": repr(ex)[:200]}
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "frac": (achieved / peak) if (achieved and peak) else None,
+                "traffic": filter_traffic_bytes(n, ne, slices),
+                "work": "algorithmic: 8 n^2 flops per column and degree step (complex HEMM), "
+                        f"{8.0 * n * n * ne:.4g} flops per full-width launch",
                 "algorithmic_bytes_per_launch": 2.0 * 2 * slices * n * n + 2.0 * 3 * slices * ne * n + 3 * 16.0 * n * ne,
                 "kernel": f"oz_gemm_kernel<S={slices},exact levels=5,complex> (bf16 split products, "
                           f"{pairs} digit pairs per complex product)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)",
                 "launch_ms_avg": kern_ms / max(1, kern_launches), "launches": kern_launches,
-                "algorithmic_flops_per_matvec": 8.0 * pairs * n * n}
+                "emulation": {"split_bf16_tflops": split_tflops, "frac": (split_tflops / peak) if (split_tflops and peak)
+                              else None, "digit_pairs": pairs,
+                              "note": "bf16 work of the split products (digit pairs x algorithmic) over the same time"},
+                "fp64_units": fp64_units}
     one.close()
 
     # end to end through the C ABI with host buffers: every step hands chase_solve pinned host A, V0, L0

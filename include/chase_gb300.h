@@ -98,6 +98,20 @@ typedef struct {
 /* Kernel launches made by this library in this process so far (all contexts). */
 int64_t chase_kernel_launch_count(void);
 
+/* Testing hook (not part of Algorithm 1): wall-clock limit, in nanoseconds, of every grid-barrier wait
+ * of the persistent Jacobi sweep kernel of the Rayleigh-Ritz eigensolve, for launches made after the
+ * call (process-wide).  0 restores the default of 2 s.  A wait that reaches the limit makes every block
+ * of the launch return and the call that launched it return CHASE_ERR_TIMEOUT; the context stays
+ * usable.  Lets a test make a wait expire without faulting or hanging the GPU. */
+void chase_set_wait_limit_ns(uint64_t ns);
+
+/* FP64 throughput probe (not part of Algorithm 1): the rate of this device's FP64 units, the
+ * denominators the FP64 filter is compared against.  which = 0: DFMA (fma.rn.f64 on the CUDA cores),
+ * which = 1: DMMA (mma.sync m8n8k4 f64 on the tensor cores).  One timed launch over every SM after a
+ * warm-up launch (CUDA events); *tflops_out = 2 x FMAs / time, *ms_out (nullable) the launch time.
+ * Runs on its own stream of the current device and returns when it has finished. */
+chase_status chase_measure_fp64_peak(int which, double* tflops_out, double* ms_out);
+
 /* Fill *opts with defaults. */
 void chase_default_opts(chase_opts* opts);
 
@@ -210,9 +224,10 @@ chase_status chase_heevj(chase_ctx* ctx, const void* G_dev, int64_t ldg, int k, 
  * Scratch is one fixed array in the library's device memory (about 2.1 MB per
  * device, held until the process exits): k > CHASE_HEEVJ_NOALLOC_KMAX returns
  * CHASE_ERR_ARG; calls that overlap on the GPU share it and race; it keeps the
- * previous call's contents (the solver writes all it reads).  The first call on
- * a device looks up the array's address on that device; make it before any
- * stream capture.  Errors are returned as statuses only (no message). */
+ * previous call's contents (the solver writes all it reads).  The first call in
+ * a CUDA context (normally a device's primary context) looks up the array's
+ * address in that context and caches it per context; make it before any stream
+ * capture.  Errors are returned as statuses only (no message). */
 chase_status chase_heevj_noalloc(const void* G_dev, int64_t ldg, int k, chase_dtype dtype, double* w_host,
                                  void* Z_dev, int64_t ldz, void* stream);
 

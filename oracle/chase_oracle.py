@@ -342,16 +342,19 @@ def qr_step(Yhat: np.ndarray, Vhat: np.ndarray) -> np.ndarray:
 # Algorithm 1, lines 6-7: Rayleigh-Ritz and residuals
 # --------------------------------------------------------------------------
 
-def rayleigh_ritz(A: np.ndarray, Qk: np.ndarray):
+def rayleigh_ritz(A: np.ndarray, Qk: np.ndarray, small_eigh=None):
     """G = Qk^H A Qk, G = Z diag(w) Z^H (ascending), Vhat = Qk Z (Algorithm 1, line 6).
 
     Reading: the projection is over the k active columns (the paper's
-    "nev x nev" is read as the active-block size).
+    "nev x nev" is read as the active-block size).  The small problem goes to a
+    standard dense solver, as the paper does (e.g. Divide & Conquer): the textbook
+    Jacobi above by default, or LAPACK's eigh passed as ``small_eigh`` (both
+    pinned against each other) where k is large enough to make Jacobi in Python slow.
     """
     W = A @ Qk
     G = np.conj(Qk.T) @ W
     G = 0.5 * (G + np.conj(G.T))
-    w, Z = jacobi_eigh(G)
+    w, Z = (small_eigh or jacobi_eigh)(G)
     return w, Qk @ Z
 
 
@@ -418,11 +421,12 @@ class SolveResult:
     converged: bool
     lanczos: LanczosResult
     history: list = field(default_factory=list)
+    block: np.ndarray | None = None   # final search block: locked pairs ascending, then the active rest
 
 
 def chase_solve(A: np.ndarray, nev: int, nex: int, tol: float, deg: int, maxdeg: int,
                 V0: np.ndarray, lanczos_starts: np.ndarray, lanczos_steps: int = 25,
-                maxiter: int = 30) -> SolveResult:
+                maxiter: int = 30, small_eigh=None) -> SolveResult:
     """Algorithm 1 (ChASE) on a dense Hermitian A, start block V0 (n x (nev+nex)).
 
     Convergence test: residual <= tol * ||A||_est with ||A||_est = max(|mu_1|, |theta_max|)
@@ -451,7 +455,7 @@ def chase_solve(A: np.ndarray, nev: int, nex: int, tol: float, deg: int, maxdeg:
         matvecs += mv
         Q = qr_step(Yhat, Vf)
         l = Yhat.shape[1]
-        w, Vr = rayleigh_ritz(A, Q[:, l:])
+        w, Vr = rayleigh_ritz(A, Q[:, l:], small_eigh)
         res = residuals(A, Vr, w)
         p = lock_prefix(res, thresh)
         Yhat = np.concatenate([Yhat, Vr[:, :p]], axis=1)
@@ -469,8 +473,12 @@ def chase_solve(A: np.ndarray, nev: int, nex: int, tol: float, deg: int, maxdeg:
                          max_res=float(res.max()) if res.size else 0.0))
         if w.size == 0:
             break
-    order = np.argsort(Lam, kind="stable")[:nev]
-    return SolveResult(Lam[order], Yhat[:, order], it, matvecs, Yhat.shape[1] >= nev, lz, hist)
+    order = np.argsort(Lam, kind="stable")
+    # the search block a correlated next problem restarts from (warm start): locked pairs ascending,
+    # then the remaining active vectors
+    block = np.concatenate([Yhat[:, order], Vhat], axis=1)
+    order = order[:nev]
+    return SolveResult(Lam[order], Yhat[:, order], it, matvecs, Yhat.shape[1] >= nev, lz, hist, block)
 
 
 # --------------------------------------------------------------------------

@@ -203,6 +203,19 @@ class ChaseEigh(torch.autograd.Function):
         return (gA,) + (None,) * 10
 
 
+def measure_fp64_peak(which: str = "dfma") -> float:
+    """Measured FP64 rate of this device in TFLOP/s: "dfma" (CUDA cores) or "dmma" (tensor cores)."""
+    lib = L.load()
+    out, ms = C.c_double(), C.c_double()
+    L.check(None, lib.chase_measure_fp64_peak(0 if which == "dfma" else 1, C.byref(out), C.byref(ms)))
+    return float(out.value)
+
+
+def set_wait_limit_ns(ns: int) -> None:
+    """Testing hook: wall-clock limit of the Jacobi sweep kernel's grid-barrier waits (0: default 2 s)."""
+    L.load().chase_set_wait_limit_ns(int(ns))
+
+
 def kernel_launch_count() -> int:
     """Kernel launches made by the library in this process so far."""
     return int(L.load().chase_kernel_launch_count())

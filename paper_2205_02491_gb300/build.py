@@ -23,10 +23,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
 
 
 def sources():
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    if any(os.path.basename(s) == "oz_gemm.cu" for s in srcs):
-        srcs = [s for s in srcs if os.path.basename(s) != "oz_stub.cu"]
-    return srcs
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
 def _compile(src: str, verbose: bool) -> str:

@@ -303,8 +303,10 @@ template <typename T> void hermitianize(cudaStream_t st, int k, T* G, int64_t ld
 // ============================================================== Cholesky and TRSM
 constexpr int CB = 32;  // block size of the blocked Cholesky / TRSM
 
-// Unblocked Cholesky of one CB x CB diagonal block in shared memory (lower).
-template <typename T> __global__ void potrf_diag_kernel(int nb, T* G, int64_t ldg, int* info, int col0) {
+// Unblocked Cholesky of one CB x CB diagonal block in shared memory (lower).  A pivot <= floor (or not
+// finite) marks the factorisation failed.
+template <typename T>
+__global__ void potrf_diag_kernel(int nb, T* G, int64_t ldg, int* info, int col0, double floor) {
   using s = S<T>;
   __shared__ T a[CB][CB + 1];
   __shared__ int bad;
@@ -315,7 +317,7 @@ template <typename T> __global__ void potrf_diag_kernel(int nb, T* G, int64_t ld
   for (int c = 0; c < nb; ++c) {
     if (i == c && j == c) {
       double d = s::re(a[c][c]);
-      if (!(d > 0.0) || !isfinite(d)) {
+      if (!(d > floor) || !isfinite(d)) {
         bad = 1;
         d = 1.0;
       }
@@ -361,11 +363,12 @@ __global__ void trsm_rows_kernel(int64_t rows, int nb, T* X, int64_t ldx, const 
 }
 
 template <typename T>
-void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems) {
+void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems,
+                 double pivot_floor) {
   for (int j0 = 0; j0 < k; j0 += CB) {
     int nb = std::min(CB, k - j0);
     T* Gjj = G + j0 + (int64_t)j0 * ldg;
-    potrf_diag_kernel<T><<<1, dim3(CB, CB), 0, st>>>(nb, Gjj, ldg, info, j0);
+    potrf_diag_kernel<T><<<1, dim3(CB, CB), 0, st>>>(nb, Gjj, ldg, info, j0, pivot_floor);
     CHASE_CHECK_LAUNCH();
     int rest = k - j0 - nb;
     if (rest <= 0) break;
@@ -555,7 +558,7 @@ template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda
   template void scale_cols<T>(cudaStream_t, int64_t, int, T*, int64_t, const double*, int);                       \
   template void add_diag<T>(cudaStream_t, int, T*, int64_t, const double*, double);                               \
   template void hermitianize<T>(cudaStream_t, int, T*, int64_t);                                                  \
-  template void potrf_lower<T>(cudaStream_t, int, T*, int64_t, int*, T*, int64_t);                                \
+  template void potrf_lower<T>(cudaStream_t, int, T*, int64_t, int*, T*, int64_t, double);                                \
   template void trsm_right_lh<T>(cudaStream_t, int64_t, int, T*, int64_t, const T*, int64_t, T*, int64_t);        \
   template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int); \
   template void zero_upper<T>(cudaStream_t, int, T*, int64_t);                                                    \

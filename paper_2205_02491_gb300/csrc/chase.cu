@@ -30,6 +30,7 @@ using namespace chase;
 
 namespace chase {
 std::atomic<long long> g_kernel_launches{0};
+std::atomic<unsigned long long> g_wait_limit_ns{0};
 }
 
 struct chase_ctx {
@@ -203,7 +204,9 @@ template <typename T> struct Solver {
 
   // C(n x k) = A(n x n) * B(n x k) with epilogue, in the given filter arithmetic.
   void hemm(const T* A, int64_t n, int64_t lda, const T* B, int64_t ldb, int k, const Epi& e, int mode) {
-    if (mode == CHASE_FP64_NATIVE || !oz::available()) {
+    CHASE_REQUIRE(mode == CHASE_FP64_NATIVE || oz::available(), CHASE_ERR_UNSUPPORTED,
+                  "the split tensor-core products need an sm_103 device; only CHASE_FP64_NATIVE runs here");
+    if (mode == CHASE_FP64_NATIVE) {
       gemm_f64<T>(st(), OP_N, OP_N, n, k, n, A, lda, B, ldb, e, W(), c->work_elems);
     } else {
       oz::prepare_A<T>(st(), c->ozw, A, n, lda, mode);  // cached per A within a call
@@ -329,7 +332,10 @@ template <typename T> struct Solver {
         add_diag<T>(st(), k, Gm, k, nullptr, shift);
       }
       CHASE_CUDA(cudaMemsetAsync(c->info, 0, sizeof(int), st()));
-      potrf_lower<T>(st(), k, Gm, k, c->info, W(), c->work_elems);
+      // the columns have unit norm, so the Gram matrix has a unit diagonal: a pivot below 8 k u means
+      // cond(X) above about (8 k u)^(-1/2), where one Cholesky-QR pass no longer yields a basis that a
+      // second pass can repair (numerically rank deficient); that pass counts as failed
+      potrf_lower<T>(st(), k, Gm, k, c->info, W(), c->work_elems, 8.0 * k * 1.1102230246251565e-16);
       int info = 0;
       CHASE_CUDA(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, st()));
       CHASE_CUDA(cudaStreamSynchronize(st()));
@@ -436,8 +442,10 @@ template <typename T> struct Solver {
     try {
       heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40, false, true);
     } catch (const Error& e) {
-      if (e.status != CHASE_ERR_NAN && e.status != CHASE_ERR_TIMEOUT) throw;
-      return false;  // G itself is untouched: the FP64 solver takes over
+      // non-finite FP32 values: G itself is untouched and the FP64 solver takes over; a grid barrier
+      // that hit its wait limit is reported as CHASE_ERR_TIMEOUT
+      if (e.status != CHASE_ERR_NAN) throw;
+      return false;
     }
     convert_mat<F, T>(st(), k, Zf, k, Z, k);
     dbg_finite(Z, k, k, k, sizeof(T), "Z after the FP32 pass");
@@ -653,8 +661,8 @@ template <typename T> struct Solver {
     CHASE_REQUIRE(tol > 0.0 && deg >= 1 && deg <= c->opts.maxdeg, CHASE_ERR_ARG, "tol or deg out of range");
     CHASE_REQUIRE(A && V0 && L0, CHASE_ERR_ARG, "null A, V0 or L0");
     CHASE_REQUIRE(mode >= CHASE_FP64 && mode <= CHASE_BF16x6, CHASE_ERR_ARG, "unknown mode");
-    CHASE_REQUIRE(mode == CHASE_FP64_NATIVE || mode == CHASE_FP64 || oz::available(), CHASE_ERR_UNSUPPORTED,
-                  "split-BF16 modes need the tensor-core kernels");
+    CHASE_REQUIRE(mode == CHASE_FP64_NATIVE || oz::available(), CHASE_ERR_UNSUPPORTED,
+                  "the FP64 and split-BF16 modes need the tensor-core kernels (sm_103); use CHASE_FP64_NATIVE");
     c->have_result = false;
     c->stats = chase_stats_t{};
     oz::invalidate(c->ozw);  // A may hold new values at the same address
@@ -1019,6 +1027,8 @@ void chase_destroy(chase_ctx* c) {
 const char* chase_last_error(const chase_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int64_t chase_kernel_launch_count(void) { return (int64_t)chase::g_kernel_launches.load(); }
+
+void chase_set_wait_limit_ns(uint64_t ns) { chase::g_wait_limit_ns.store((unsigned long long)ns); }
 
 // true for memory the device cannot be handed directly as a kernel argument of this library:
 // pageable or pinned host allocations (copied to the device first)

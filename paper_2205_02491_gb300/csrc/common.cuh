@@ -150,6 +150,14 @@ extern std::atomic<long long> g_kernel_launches;
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// Wall-clock limit of the bounded grid-barrier waits of the Jacobi sweep kernel (nanoseconds).  Two
+// seconds unless a test shortens it through chase_set_wait_limit_ns (0 restores the default).
+extern std::atomic<unsigned long long> g_wait_limit_ns;
+inline unsigned long long grid_wait_limit_ns() {
+  const unsigned long long v = g_wait_limit_ns.load();
+  return v ? v : 2000000000ull;
+}
+
 // warp-level FP64 sum
 __device__ inline double warp_sum(double v) {
 #pragma unroll

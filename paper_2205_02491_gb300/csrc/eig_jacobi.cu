@@ -198,7 +198,6 @@ __global__ void jacobi_apply_z_kernel(int k, int kp, int r, T* Z, int64_t ldz, c
 // updates, separated by grid-wide barriers (all blocks are co-resident under a cooperative
 // launch).  Every barrier wait is bounded by a wall-clock limit; on expiry, or when another block
 // has flagged an error, the block sets/keeps the error flag and returns.
-constexpr unsigned long long GRID_WAIT_NS = 2000000000ull;
 constexpr int SWEEP_THREADS = 256;  // up to four blocks per SM (measured faster than one 1024-thread block)
 // barrier words, each in its own 32-byte sector so that the pollers of the generation word do not
 // contend with the arrival atomics
@@ -210,8 +209,9 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-// bar[BAR_COUNT]: arrivals, bar[BAR_GEN]: generation, bar[BAR_ERR]: error flag (all zero at launch)
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+// bar[BAR_COUNT]: arrivals, bar[BAR_GEN]: generation, bar[BAR_ERR]: error flag (all zero at launch);
+// wait_ns: wall-clock limit of one wait
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned long long wait_ns) {
   __shared__ int ok_sh;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -231,7 +231,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
             ok = 0;
             break;
           }
-          if (gtimer() - t0 > GRID_WAIT_NS) {
+          if (gtimer() - t0 > wait_ns) {
             atomicOr(&bar[BAR_ERR], 1u);
             ok = 0;
             break;
@@ -249,17 +249,18 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
 
 template <typename T>
 __global__ void __launch_bounds__(SWEEP_THREADS, 4) jacobi_sweep_kernel(int k, int kp, T* G, int64_t ldg, T* Z,
-                                                                        int64_t ldz, Rot<T>* rot, unsigned* bar) {
+                                                                        int64_t ldz, Rot<T>* rot, unsigned* bar,
+                                                                        unsigned long long wait_ns) {
   const int half = kp / 2;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   const int64_t ng = (int64_t)half * half, nz = (int64_t)k * half;
   for (int r = 0; r < kp - 1; ++r) {
     for (int64_t idx = tid; idx < half; idx += nthr) jacobi_params<T>(k, kp, r, (int)idx, G, ldg, rot);
-    if (!grid_barrier(bar, gridDim.x)) return;
+    if (!grid_barrier(bar, gridDim.x, wait_ns)) return;
     for (int64_t x = tid; x < ng; x += nthr) jacobi_apply_g<T>(k, kp, r, (int)(x % half), (int)(x / half), G, ldg, rot);
     for (int64_t x = tid; x < nz; x += nthr) jacobi_apply_z<T>(k, kp, r, (int)(x % k), (int)(x / k), Z, ldz, rot);
-    if (!grid_barrier(bar, gridDim.x)) return;
+    if (!grid_barrier(bar, gridDim.x, wait_ns)) return;
   }
 }
 
@@ -393,7 +394,8 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
       T* Gp = G;
       T* Zp = Zu;
       Rot<T>* rp = rot;
-      void* args[] = {&kk, &kpp, &Gp, &ldgg, &Zp, &ldzz, &rp, &bar};
+      unsigned long long wait_ns = grid_wait_limit_ns();
+      void* args[] = {&kk, &kpp, &Gp, &ldgg, &Zp, &ldzz, &rp, &bar, &wait_ns};
       CHASE_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel<T>, dim3(coop_grid), dim3(SWEEP_THREADS),
                                              args, 0, st));
       CHASE_CHECK_LAUNCH();

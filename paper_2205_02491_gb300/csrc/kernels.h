@@ -35,9 +35,11 @@ template <typename T> void scale_cols(cudaStream_t st, int64_t n, int k, T* X, i
 template <typename T>
 void copy_cols(cudaStream_t st, int64_t n, int k, const T* src, int64_t lds, T* dst, int64_t ldd);
 
-// Cholesky G = L L^H (lower, in place, k x k).  info: device int, set > 0 on a non-positive pivot.
+// Cholesky G = L L^H (lower, in place, k x k).  info: device int, set > 0 on a pivot <= pivot_floor
+// (0: only non-positive pivots fail).
 template <typename T>
-void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems);
+void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems,
+                 double pivot_floor = 0.0);
 // X <- X L^{-H} (right solve with the lower Cholesky factor), X n x k.
 template <typename T>
 void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T* L, int64_t ldl, T* work,

@@ -17,9 +17,14 @@
 //     (one stream, or events).  The array keeps the previous call's contents;
 //     the solver writes every scratch value it reads, so nothing needs clearing.
 //   * Host code cannot use the array's symbol as a device address.  The first
-//     call on each device looks up the array's device address with
-//     cudaGetSymbolAddress while that device is current and caches it; make
-//     that first call before capturing any stream into a CUDA graph.
+//     call in each CUDA context (normally one per device: the primary context)
+//     looks up the array's device address with cudaGetSymbolAddress while that
+//     context is current and caches it by context, so a context created later
+//     on the same device (after cudaDeviceReset, or a caller's own context)
+//     gets its own lookup; make the first call in a context before capturing
+//     any stream into a CUDA graph.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "../../include/chase_gb300.h"
@@ -36,9 +41,28 @@ constexpr size_t SCRATCH_BYTES = SCALARS * 16 + (3 * (size_t)KMAX + 16) * 8 + (s
 
 __device__ __align__(256) unsigned char g_heevj_scratch[SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
+// (context, address) pairs; a context's module, and with it the array, lives as long as the context
+constexpr int MAX_CONTEXTS = 64;
 std::mutex g_mu;
-void* g_addr[MAX_DEVICES] = {};
+CUcontext g_ctx[MAX_CONTEXTS] = {};
+void* g_addr[MAX_CONTEXTS] = {};
+int g_used = 0;
+
+// cuCtxGetCurrent through the runtime's driver entry-point query, so that the library does not link
+// the driver library (it loads on machines without a GPU driver)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetCurrentFn)p;
+  });
+  return fn;
+}
 
 template <typename T>
 void run(const T* G, int64_t ldg, int k, double* w_host, T* Z, int64_t ldz, cudaStream_t st, unsigned char* base) {
@@ -62,19 +86,31 @@ extern "C" chase_status chase_heevj_noalloc(const void* G_dev, int64_t ldg, int 
       (dtype != CHASE_R64 && dtype != CHASE_C128))
     return CHASE_ERR_ARG;
   try {
-    int dev = 0;
-    CHASE_CUDA(cudaGetDevice(&dev));
-    CHASE_REQUIRE(dev >= 0 && dev < MAX_DEVICES, CHASE_ERR_ARG, "device index out of range");
+    CtxGetCurrentFn get_ctx = ctx_get_current();
+    if (!get_ctx) return CHASE_ERR_CUDA;
+    CUcontext cur = nullptr;
+    if (get_ctx(&cur) != CUDA_SUCCESS) return CHASE_ERR_CUDA;
+    if (cur == nullptr) {
+      // no context yet: the runtime's symbol lookup creates the device's primary context
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_heevj_scratch) != cudaSuccess) return CHASE_ERR_CUDA;
+      if (get_ctx(&cur) != CUDA_SUCCESS || cur == nullptr) return CHASE_ERR_CUDA;
+    }
     unsigned char* base = nullptr;
     {
       std::lock_guard<std::mutex> lock(g_mu);
-      if (!g_addr[dev]) {
+      for (int i = 0; i < g_used && !base; ++i)
+        if (g_ctx[i] == cur) base = (unsigned char*)g_addr[i];
+      if (!base) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_heevj_scratch);
         if (e != cudaSuccess) return CHASE_ERR_CUDA;
-        g_addr[dev] = p;
+        // a full table (more than 64 contexts in one process) overwrites its first entry
+        const int slot = g_used < MAX_CONTEXTS ? g_used++ : 0;
+        g_ctx[slot] = cur;
+        g_addr[slot] = p;
+        base = (unsigned char*)p;
       }
-      base = (unsigned char*)g_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == CHASE_C128)

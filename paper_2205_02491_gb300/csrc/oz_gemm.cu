@@ -15,8 +15,9 @@
 //   the whole K.  Each tensor-core accumulation step truncates to about 24 bits
 //   of the running sum (measured), so the error of a shared accumulator grows
 //   with the number of steps times its magnitude; keeping five levels exact
-//   leaves only terms below 2^-40 there.  Truncation after level S-1 is below 2^-(8S-8) relative
-//   to |row max| * |col max| per product (S = 7: 2^-56, errors comparable to DFMA).
+//   leaves only terms below 2^-40 there.  The digits dropped after slice S-1 of each operand (and the
+//   pairs beyond level S-1) leave a truncation below about 2^-8S relative to |row max| * |col max| per
+//   product (S = 7: 2^-56, errors comparable to DFMA).
 //   Mixed modes (S = 2: 3 products, S = 3: 6 products): one FP32 accumulator.
 //
 // Complex operands use real tiles: with B1 = [Yr | Yi] and B2 = [-Yi | Yr]

@@ -109,3 +109,22 @@ def test_backward_c5_gradient_check(pkg):
     Vb[:, :64] = gV
     ref = O._dense_grad(lam, Vall, gl, Vb)
     assert np.max(np.abs(gA - ref)) <= 1e-6 * np.max(np.abs(ref))
+
+
+def test_backward_c5_central_differences(pkg):
+    """The n = 4096 differentiation workload checked as the gradient check is set: the GPU forward at
+    tol 1e-13 (about the FP64 floor there) and the hand-written backward, against central differences
+    (h = 1e-6) of the exact loss along 8 seeded symmetric directions, to 1e-6 relative."""
+    p = G.problem_c5(4096)
+    A = p.dense()
+    w, Bm = p.extra["w"], p.extra["B"]
+    L, gA, _ = _gpu_grad(pkg, p, A, w, Bm, tol=1e-13, minres_tol=1e-12)
+    assert abs(L - _exact_loss(A, 64, w, Bm)) <= 1e-9 * abs(L)
+    g = G.rng(5, 0, 9)
+    h = 1e-6
+    for _ in range(8):
+        D = g.standard_normal(A.shape)
+        D = 0.5 * (D + D.T)
+        fd = (_exact_loss(A + h * D, 64, w, Bm) - _exact_loss(A - h * D, 64, w, Bm)) / (2 * h)
+        an = float(np.sum(gA * D))
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)

@@ -3,6 +3,7 @@ import numpy as np
 import pytest
 
 from gen import problems as G
+from oracle import chase_oracle as O
 from tests.helpers import dev, host
 
 pytestmark = pytest.mark.gpu
@@ -97,4 +98,43 @@ def test_batched_rejects_oversize_problem(pkg):
     with pytest.raises(pkg.ChaseError) as e:
         ctx.solve_batched([dev(p.dense())], [p.nev], [p.nex], 1e-10, 20, "fp64", [dev(p.V0)], [dev(p.L0)])
     assert e.value.status == 1
+    ctx.close()
+
+
+def test_batched_c4_subset_vs_oracle(pkg):
+    """Problems of the 64-problem batched workload at their own sizes (n = 4155 and n = 568, nev 5% of n,
+    nex nev/2), two steps of the correlated sequence: the cold step from the seeded block, then
+    A += 1e-3 H and a warm start from each side's own previous search block.  Eigenvalues, residuals and
+    iteration counts against the CPU oracle run the same way (its small eigensolves by LAPACK)."""
+    pids = [41, 19]
+    probs = [G.problem_c4(pid) for pid in pids]
+    assert probs[0].n >= 4096 and probs[1].n <= 600
+    ctx = pkg.Chase(max(p.n for p in probs), max(p.ne for p in probs), complex_=True,
+                    opts={"batch_workers": 2})
+    A_host = [p.dense() for p in probs]
+    A_dev = [dev(a) for a in A_host]
+    V = [dev(p.V0) for p in probs]
+    L0 = [dev(p.L0) for p in probs]
+    blocks = [p.V0 for p in probs]
+    for step in range(2):
+        ws, stats = ctx.solve_batched(A_dev, [p.nev for p in probs], [p.nex for p in probs], 1e-10, 20, "fp64",
+                                      V, L0)
+        for q, p in enumerate(probs):
+            ref = O.chase_solve(A_host[q], p.nev, p.nex, 1e-10, 20, 36, blocks[q], p.L0, 25,
+                                small_eigh=np.linalg.eigh)
+            assert ref.converged
+            nrm = p.norm2() * (1 + 2e-3)      # |lam| <= 1, plus the perturbations
+            w = ws[q].cpu().numpy()
+            assert np.max(np.abs(w - ref.eigvals)) <= 1e-10 * nrm
+            if step == 0:
+                assert np.max(np.abs(w - p.lam[: p.nev])) <= 1e-10 * nrm
+            Vq = host(V[q])[:, : p.nev]
+            R = A_host[q] @ Vq - Vq * w[None, :]
+            assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
+            assert abs(stats[q]["iterations"] - ref.iterations) <= 1
+            blocks[q] = ref.block
+        for q, p in enumerate(probs):
+            seed = G.sequence_seed(pids[q], step)
+            ctx.perturb(A_dev[q], 1e-3, seed)
+            A_host[q] = A_host[q] + 1e-3 * G.perturbation(p.n, seed, True)
     ctx.close()

@@ -42,7 +42,7 @@ def test_hemm_fp64_split_complex(pkg, n, k):
     s = pkg.Chase(n, k, complex_=True)
     C = host(s.hemm(dev(A), dev(B), "fp64"))
     ref = _exact(A, B)
-    assert _rel_err(C, ref, A, B) <= 2.0 ** -49
+    assert _rel_err(C, ref, A, B) <= 2.0 ** -53
 
 
 @pytest.mark.parametrize("n,k", [(257, 200), (64, 3)])
@@ -55,7 +55,7 @@ def test_hemm_fp64_split_real(pkg, n, k):
     ref = (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
     ra = np.max(np.abs(A), axis=1)
     cb = np.max(np.abs(B), axis=0)
-    assert np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / n <= 2.0 ** -49
+    assert np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / n <= 2.0 ** -53
 
 
 def test_exact_levels_at_worst_case_sums(pkg):

@@ -505,3 +505,18 @@ def test_backward_eigenvalue_only_is_v_diag_vt():
     w = g.standard_normal(nev)
     Ab = O.eig_backward(A, lam_c, V, w, np.zeros((n, nev)))
     assert np.max(np.abs(Ab - V @ np.diag(w) @ V.T)) <= 1e-14
+
+
+def test_solve_with_lapack_small_eigensolver_matches_jacobi():
+    """The Rayleigh-Ritz step accepts LAPACK's eigh as its dense solver (used by large GPU parity tests);
+    it reaches the same eigenpairs, iterations and final search block span as the textbook Jacobi."""
+    p = G.problem_small(120, 8, 6, complex_=True, seed_pid=17)
+    A = p.dense()
+    r1 = O.chase_solve(A, p.nev, p.nex, 1e-10, 20, 36, p.V0, p.L0, 25)
+    r2 = O.chase_solve(A, p.nev, p.nex, 1e-10, 20, 36, p.V0, p.L0, 25, small_eigh=np.linalg.eigh)
+    assert r1.converged and r2.converged
+    assert np.max(np.abs(r1.eigvals - r2.eigvals)) <= 1e-12
+    assert abs(r1.iterations - r2.iterations) <= 1
+    assert r1.block.shape == (120, p.ne) and r2.block.shape == (120, p.ne)
+    # the block starts with the eigenvectors, ascending
+    assert np.allclose(r1.block[:, :p.nev], r1.eigvecs, atol=0)

@@ -9,8 +9,8 @@ The claims checked here:
   chunk of 96 K values stays below 2^24 for L <= 4 and is exact in FP32;
 - the exact levels 0..4 of one product add up to at most 2^14 (1 + 2^-29) in level-0 units, so their int64
   accumulation in units of 2^-32 cannot overflow for K <= 65472 (and that limit is tight);
-- the level-by-level product equals the FP64 product to 2^-49 per K term (the parity tests' bound) when levels
-  0..4 are exact and the rest are rounded;
+- the level-by-level product equals the FP64 product to 2^-53 per K term (FP64's unit roundoff, the parity
+  tests' bound) when levels 0..4 are exact and the rest are rounded, and one slice fewer (S = 6) misses it;
 - the mixed modes (2 or 3 slices, one rounded accumulator) meet the per-term bounds 2^-13 and 2^-20.
 """
 import numpy as np
@@ -149,7 +149,10 @@ def test_level_product_meets_the_fp64_parity_bound():
     ref = (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
     ra = np.max(np.abs(A), axis=1)
     cb = np.max(np.abs(B), axis=0)
-    assert np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / K <= 2.0 ** -49
+    assert np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / K <= 2.0 ** -53
+    # the bound is tight enough to catch a precision regression: six slices (truncation 2^-48) miss it
+    C6 = _split_product(A, B, S_FP64 - 1, NEX)
+    assert np.max(np.abs(C6 - ref) / (ra[:, None] * cb[None, :])) / K > 2.0 ** -53
 
 
 @pytest.mark.parametrize("S,bound", [(2, 2.0 ** -13), (3, 2.0 ** -20)])
