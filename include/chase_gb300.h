@@ -93,6 +93,8 @@ typedef struct {
   int minres_iterations;        /* MINRES iterations of the last chase_backward */
   int rr_clusters;              /* eigenvalue clusters solved exactly in the Rayleigh-Ritz eigensolves */
   int rr_fallbacks;             /* Rayleigh-Ritz eigensolves that fell back to the FP64 Jacobi */
+  int qr_replaced;              /* numerically dependent columns of filtered blocks that the QR step
+                                   replaced by seeded random vectors */
 } chase_stats_t;
 
 /* Kernel launches made by this library in this process so far (all contexts). */
@@ -195,7 +197,9 @@ chase_status chase_filter(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t 
 
 /* Algorithm 1, line 5: orthonormalise X (n x ncols, ld ldx) in place by
  * Cholesky-QR2 (shifted Cholesky-QR3 fallback); the first nlocked columns are
- * assumed orthonormal and are left unchanged. */
+ * assumed orthonormal and are left unchanged.  A column whose remainder after
+ * the columns before it is at rounding level (numerically dependent) is first
+ * replaced by a seeded random vector (counted in chase_stats_t.qr_replaced). */
 chase_status chase_qr(chase_ctx* ctx, void* X_dev, int64_t n, int64_t ldx, int ncols, int nlocked);
 
 /* Algorithm 1, lines 6-7: Rayleigh-Ritz on the ncols orthonormal columns Q

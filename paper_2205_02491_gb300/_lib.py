@@ -39,7 +39,8 @@ class Stats(C.Structure):
                 ("max_resid", C.c_double), ("qr_fallbacks", C.c_int), ("filter_launches", C.c_int),
                 ("ms_filter_kernel", C.c_double), ("filter_kernel_launches", C.c_int),
                 ("ms_filter_kernel_lowp", C.c_double), ("ms_backward", C.c_double),
-                ("minres_iterations", C.c_int), ("rr_clusters", C.c_int), ("rr_fallbacks", C.c_int)]
+                ("minres_iterations", C.c_int), ("rr_clusters", C.c_int), ("rr_fallbacks", C.c_int),
+                ("qr_replaced", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

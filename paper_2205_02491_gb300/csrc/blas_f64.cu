@@ -303,40 +303,55 @@ template <typename T> void hermitianize(cudaStream_t st, int k, T* G, int64_t ld
 // ============================================================== Cholesky and TRSM
 constexpr int CB = 32;  // block size of the blocked Cholesky / TRSM
 
-// Unblocked Cholesky of one CB x CB diagonal block in shared memory (lower).  A pivot <= floor (or not
-// finite) marks the factorisation failed.
+// Unblocked Cholesky of one CB x CB diagonal block in shared memory (lower).  A pivot that is not finite,
+// or <= floor, marks the factorisation failed (info), except in detection mode (dep != null): there a
+// finite pivot <= floor marks its column numerically dependent on the columns before it (dep[1 + col],
+// count in dep[0]); the column gets a unit pivot and a zero column below it, so it drops out of the
+// trailing update and the factorisation of the other columns goes on.
 template <typename T>
-__global__ void potrf_diag_kernel(int nb, T* G, int64_t ldg, int* info, int col0, double floor) {
+__global__ void potrf_diag_kernel(int nb, T* G, int64_t ldg, int* info, int col0, double floor, int* dep) {
   using s = S<T>;
   __shared__ T a[CB][CB + 1];
   __shared__ int bad;
+  __shared__ int dep_sh[CB];
   int i = threadIdx.x, j = threadIdx.y;  // element (i, j)
   if (i == 0 && j == 0) bad = 0;
+  if (j == 0 && i < CB) dep_sh[i] = 0;
   if (i < nb && j < nb) a[i][j] = G[i + j * ldg];
   __syncthreads();
   for (int c = 0; c < nb; ++c) {
     if (i == c && j == c) {
       double d = s::re(a[c][c]);
-      if (!(d > floor) || !isfinite(d)) {
+      if (!isfinite(d)) {
         bad = 1;
+        d = 1.0;
+      } else if (!(d > floor)) {
+        if (dep) dep_sh[c] = 1;
+        else bad = 1;
         d = 1.0;
       }
       a[c][c] = s::make(sqrt(d), 0.0);
     }
     __syncthreads();
     double piv = s::re(a[c][c]);
-    if (j == c && i > c && i < nb) a[i][c] = s::scale(a[i][c], 1.0 / piv);
+    if (j == c && i > c && i < nb) a[i][c] = dep_sh[c] ? s::zero() : s::scale(a[i][c], 1.0 / piv);
     __syncthreads();
     if (i > c && j > c && i < nb && j <= i) a[i][j] = s::sub(a[i][j], s::mul(a[i][c], s::conj(a[j][c])));
     __syncthreads();
   }
   if (i < nb && j < nb) G[i + j * ldg] = (j <= i) ? a[i][j] : s::zero();
   if (i == 0 && j == 0 && bad && info) atomicMax(info, col0 + 1);
+  if (dep && j == 0 && i < nb && dep_sh[i]) {
+    dep[1 + col0 + i] = 1;
+    atomicAdd(&dep[0], 1);
+  }
 }
 
-// X(rows x nb) <- X L^{-H} with L the nb x nb lower block (row-parallel forward substitution).
+// X(rows x nb) <- X L^{-H} with L the nb x nb lower block (row-parallel forward substitution).  dep
+// (nullable): dependent-column flags of the block's columns, whose results are set to zero.
 template <typename T>
-__global__ void trsm_rows_kernel(int64_t rows, int nb, T* X, int64_t ldx, const T* L, int64_t ldl) {
+__global__ void trsm_rows_kernel(int64_t rows, int nb, T* X, int64_t ldx, const T* L, int64_t ldl,
+                                 const int* dep) {
   using s = S<T>;
   __shared__ T l[CB][CB + 1];
   for (int t = threadIdx.x; t < CB * CB; t += blockDim.x) {
@@ -354,7 +369,7 @@ __global__ void trsm_rows_kernel(int64_t rows, int nb, T* X, int64_t ldx, const 
 #pragma unroll
       for (int m = 0; m < CB; ++m)
         if (m < j) v = s::sub(v, s::mul(q[m], s::conj(l[j][m])));
-      q[j] = s::scale(v, 1.0 / s::re(l[j][j]));
+      q[j] = (dep && dep[j]) ? s::zero() : s::scale(v, 1.0 / s::re(l[j][j]));
     }
   }
 #pragma unroll
@@ -364,16 +379,17 @@ __global__ void trsm_rows_kernel(int64_t rows, int nb, T* X, int64_t ldx, const 
 
 template <typename T>
 void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems,
-                 double pivot_floor) {
+                 double pivot_floor, int* dep) {
   for (int j0 = 0; j0 < k; j0 += CB) {
     int nb = std::min(CB, k - j0);
     T* Gjj = G + j0 + (int64_t)j0 * ldg;
-    potrf_diag_kernel<T><<<1, dim3(CB, CB), 0, st>>>(nb, Gjj, ldg, info, j0, pivot_floor);
+    potrf_diag_kernel<T><<<1, dim3(CB, CB), 0, st>>>(nb, Gjj, ldg, info, j0, pivot_floor, dep);
     CHASE_CHECK_LAUNCH();
     int rest = k - j0 - nb;
     if (rest <= 0) break;
     T* P = G + (j0 + nb) + (int64_t)j0 * ldg;  // panel below the diagonal block
-    trsm_rows_kernel<T><<<ceil_div(rest, 128), 128, 0, st>>>(rest, nb, P, ldg, Gjj, ldg);
+    trsm_rows_kernel<T><<<ceil_div(rest, 128), 128, 0, st>>>(rest, nb, P, ldg, Gjj, ldg,
+                                                             dep ? dep + 1 + j0 : nullptr);
     CHASE_CHECK_LAUNCH();
     // trailing update  G22 -= P P^H
     T* G22 = G + (j0 + nb) + (int64_t)(j0 + nb) * ldg;
@@ -395,7 +411,7 @@ void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T
     int nb = std::min(CB, k - j0);
     T* Xb = X + (int64_t)j0 * ldx;
     const T* Ljj = L + j0 + (int64_t)j0 * ldl;
-    trsm_rows_kernel<T><<<ceil_div(n, 128), 128, 0, st>>>(n, nb, Xb, ldx, Ljj, ldl);
+    trsm_rows_kernel<T><<<ceil_div(n, 128), 128, 0, st>>>(n, nb, Xb, ldx, Ljj, ldl, nullptr);
     CHASE_CHECK_LAUNCH();
     int rest = k - j0 - nb;
     if (rest <= 0) break;
@@ -539,6 +555,28 @@ __global__ void perturb_kernel(T* A, int64_t n, int64_t lda, double eps, unsigne
   }
 }
 
+// Columns flagged in depflags (depflags[j] != 0) of X (n x k) get fresh standard (complex) Gaussian
+// entries from the counter-based generator above, counter i + j n.
+template <typename T>
+__global__ void fill_dependent_cols_kernel(int64_t n, T* X, int64_t ldx, const int* depflags, unsigned long long seed) {
+  using s = S<T>;
+  const int j = blockIdx.y;
+  if (!depflags[j]) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double2 g = normal_pair(seed, (unsigned long long)(i + (int64_t)j * n));
+    X[i + (int64_t)j * ldx] = s::cplx ? s::make(0.7071067811865476 * g.x, 0.7071067811865476 * g.y) : s::make(g.x, 0.0);
+  }
+}
+
+template <typename T>
+void fill_dependent_cols(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const int* depflags,
+                         unsigned long long seed) {
+  if (k <= 0) return;
+  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 64), (unsigned)k);
+  fill_dependent_cols_kernel<T><<<grid, 256, 0, st>>>(n, X, ldx, depflags, seed);
+  CHASE_CHECK_LAUNCH();
+}
+
 template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda, double eps, unsigned long long seed) {
   CHASE_REQUIRE(n <= 65535, 1, "perturbation supports n <= 65535");
   dim3 grid(ceil_div(n, 256), (unsigned)n);
@@ -558,7 +596,8 @@ template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda
   template void scale_cols<T>(cudaStream_t, int64_t, int, T*, int64_t, const double*, int);                       \
   template void add_diag<T>(cudaStream_t, int, T*, int64_t, const double*, double);                               \
   template void hermitianize<T>(cudaStream_t, int, T*, int64_t);                                                  \
-  template void potrf_lower<T>(cudaStream_t, int, T*, int64_t, int*, T*, int64_t, double);                                \
+  template void potrf_lower<T>(cudaStream_t, int, T*, int64_t, int*, T*, int64_t, double, int*);                   \
+  template void fill_dependent_cols<T>(cudaStream_t, int64_t, int, T*, int64_t, const int*, unsigned long long);  \
   template void trsm_right_lh<T>(cudaStream_t, int64_t, int, T*, int64_t, const T*, int64_t, T*, int64_t);        \
   template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int); \
   template void zero_upper<T>(cudaStream_t, int, T*, int64_t);                                                    \

@@ -71,6 +71,8 @@ struct chase_ctx {
   int* perm = nullptr;
   int* info = nullptr;
   int* status_dev = nullptr;
+  int* qr_dep = nullptr;             // Cholesky-QR dependent-column flags (count, then ne_max flags)
+  unsigned long long qr_fill_calls = 0;  // seeds the random refill of dependent columns
   oz::Workspace ozw{};
   // result state
   bool have_result = false;
@@ -317,7 +319,10 @@ template <typename T> struct Solver {
     // column equilibration (does not change the span)
     colnorms<T>(st(), n, k, X, ldx, c->dwork);
     scale_cols<T>(st(), n, k, X, ldx, c->dwork, 1);
-    auto chol_pass = [&](double shift_factor) -> bool {
+    // dep (nullable): detection mode of the Cholesky factorisation; returns false with *ndep > 0 when it
+    // found numerically dependent columns (X is then left unchanged)
+    int ndep = 0;
+    auto chol_pass = [&](double shift_factor, int* dep = nullptr) -> bool {
       Epi e;
       e.C = Gm;
       e.ldc = k;
@@ -332,14 +337,18 @@ template <typename T> struct Solver {
         add_diag<T>(st(), k, Gm, k, nullptr, shift);
       }
       CHASE_CUDA(cudaMemsetAsync(c->info, 0, sizeof(int), st()));
-      // the columns have unit norm, so the Gram matrix has a unit diagonal: a pivot below 8 k u means
-      // cond(X) above about (8 k u)^(-1/2), where one Cholesky-QR pass no longer yields a basis that a
-      // second pass can repair (numerically rank deficient); that pass counts as failed
-      potrf_lower<T>(st(), k, Gm, k, c->info, W(), c->work_elems, 8.0 * k * 1.1102230246251565e-16);
-      int info = 0;
-      CHASE_CUDA(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, st()));
+      // detection: the columns have unit norm, so the Gram matrix has a unit diagonal and a pivot below
+      // 8 (k + sqrt(n)) u lies within the rounding error of the Gram matrix and its factorisation: that
+      // column is numerically in the span of the columns before it
+      const double floor_dep = 8.0 * ((double)k + std::sqrt((double)n)) * 1.1102230246251565e-16;
+      if (dep) CHASE_CUDA(cudaMemsetAsync(dep, 0, (size_t)(k + 1) * sizeof(int), st()));
+      potrf_lower<T>(st(), k, Gm, k, c->info, W(), c->work_elems, dep ? floor_dep : 0.0, dep);
+      int hinfo[2] = {0, 0};
+      CHASE_CUDA(cudaMemcpyAsync(&hinfo[0], c->info, sizeof(int), cudaMemcpyDeviceToHost, st()));
+      if (dep) CHASE_CUDA(cudaMemcpyAsync(&hinfo[1], dep, sizeof(int), cudaMemcpyDeviceToHost, st()));
       CHASE_CUDA(cudaStreamSynchronize(st()));
-      if (info != 0) return false;
+      ndep = hinfo[1];
+      if (hinfo[0] != 0 || ndep > 0) return false;
       if (use_split(pm, n, k, k)) {
         // X <- X L^{-H} as one product with the explicit triangular inverse (written over X)
         zero_upper<T>(st(), k, Gm, k);
@@ -355,8 +364,22 @@ template <typename T> struct Solver {
       return true;
     };
     // Cholesky-QR2 with a projection before each pass, so the final basis is orthogonal to the
-    // locked columns to rounding even when X was ill-conditioned
-    bool ok = chol_pass(0.0);
+    // locked columns to rounding even when X was ill-conditioned.  A filtered block can be numerically
+    // rank deficient (a few eigen-directions amplified beyond 1e16 over the rest): the first pass then
+    // finds columns whose remainder after the columns before them is rounding noise.  Those columns
+    // carry no information a QR could recover; they are replaced by fresh seeded random vectors (which
+    // the next filter steps act on like any start vector) and the pass is repeated.
+    bool ok = false;
+    for (int attempt = 0;; ++attempt) {
+      ok = chol_pass(0.0, attempt < 3 ? c->qr_dep : nullptr);
+      if (ok || ndep == 0) break;
+      c->stats.qr_replaced += ndep;
+      fill_dependent_cols<T>(st(), n, k, X, ldx, c->qr_dep + 1, 0x5DEECE66DULL + 7919ULL * (++c->qr_fill_calls));
+      project();
+      colnorms<T>(st(), n, k, X, ldx, c->dwork);
+      scale_cols<T>(st(), n, k, X, ldx, c->dwork, 1);
+      ndep = 0;
+    }
     if (ok) {
       project();
       ok = chol_pass(0.0);
@@ -982,6 +1005,7 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
     CHASE_CUDA(cudaMalloc(&c->perm, ne_max * sizeof(int)));
     CHASE_CUDA(cudaMalloc(&c->info, sizeof(int)));
     CHASE_CUDA(cudaMalloc(&c->status_dev, 4 * sizeof(int)));
+    CHASE_CUDA(cudaMalloc(&c->qr_dep, (size_t)(ne_max + 1) * sizeof(int)));
     oz::create(c->ozw, n_max, ne_max, dtype == CHASE_C128, c->opts.oz_slices);
     // workers of batched solves: same sizes and options, one non-blocking stream each
     chase_opts wo = c->opts;
@@ -1014,7 +1038,7 @@ void chase_destroy(chase_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
                   c->lam_locked, c->eigvals, c->lam_sorted, c->bwd, c->bounds, c->deg, c->perm, c->info,
-                  c->status_dev, c->a_stage, c->l0_stage};
+                  c->status_dev, c->qr_dep, c->a_stage, c->l0_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   oz::destroy(c->ozw);

@@ -35,11 +35,17 @@ template <typename T> void scale_cols(cudaStream_t st, int64_t n, int k, T* X, i
 template <typename T>
 void copy_cols(cudaStream_t st, int64_t n, int k, const T* src, int64_t lds, T* dst, int64_t ldd);
 
-// Cholesky G = L L^H (lower, in place, k x k).  info: device int, set > 0 on a pivot <= pivot_floor
-// (0: only non-positive pivots fail).
+// Cholesky G = L L^H (lower, in place, k x k).  info: device int, set > 0 on a non-finite pivot or one
+// <= pivot_floor.  dep (nullable, k + 1 ints, zeroed by the caller): detection mode, where a finite pivot
+// <= pivot_floor marks its column as numerically dependent (dep[1 + j] = 1, dep[0] counts them) instead
+// of failing; such a column is decoupled (unit pivot, zero below it) and the factorisation goes on.
 template <typename T>
 void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems,
-                 double pivot_floor = 0.0);
+                 double pivot_floor = 0.0, int* dep = nullptr);
+// Columns j of X (n x k) with depflags[j] != 0 get seeded standard (complex) Gaussian entries.
+template <typename T>
+void fill_dependent_cols(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const int* depflags,
+                         unsigned long long seed);
 // X <- X L^{-H} (right solve with the lower Cholesky factor), X n x k.
 template <typename T>
 void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T* L, int64_t ldl, T* work,

@@ -24,6 +24,7 @@ struct Workspace {
   double* l_scale = nullptr;  // per-row scale of the general left operand
   double* b_scale = nullptr;  // per-column scale of the right operand
   int* flags = nullptr;       // device error flags of the bounded waits
+  int group_m = 8;            // row blocks per tile group of the split-product launch order
   // optional CUDA-event timing of the product kernels (filter roofline)
   bool timing = false;
   std::vector<cudaEvent_t> ev;

@@ -52,8 +52,10 @@ constexpr int EPI_WARP0 = 2;
 constexpr int EPI_WARPS = 8;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 
-template <int S, int NEX, bool CPLX> struct Cfg {
-  static constexpr int NT = NEX > 0 ? 80 : 128;    // accumulator width (MMA N)
+// NTT: accumulator width (MMA N).  80 for the FP64 modes (six accumulators share TMEM), 128 for the
+// single-accumulator mixed modes, 16 for narrow right operands (a few columns: the Lanczos block).
+template <int S, int NEX, bool CPLX, int NTT> struct Cfg {
+  static constexpr int NT = NTT;
   static constexpr int AP = CPLX ? 2 : 1;          // left planes per slice (re, im)
   static constexpr int BP = CPLX ? 3 : 1;          // right planes per slice (-im, re, im)
   static constexpr int NCOLS = CPLX ? NT / 2 : NT; // output columns per tile
@@ -245,13 +247,16 @@ struct EpiArgs {
 // slices of the left operand in processing order: descending, so that the
 // first MMAs of every k-block go to the inexact accumulator while the epilogue
 // flushes the exact ones
-template <int S, int NEX, bool CPLX>
+// Tiles run in groups of group_m row blocks: inside a group the row block varies fastest, so the CTAs that
+// are resident together share the right-operand column blocks (read from DRAM about once per group) and
+// a few left-operand row blocks, instead of every row block re-streaming all right-operand planes.
+template <int S, int NEX, bool CPLX, int NTT>
 // 168 registers: ten warps put three on some SM sub-partitions (16384 registers each)
 __global__ void __maxnreg__(168)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, const double* __restrict__ a_scale, const double* __restrict__ b_scale, EpiArgs ep,
-                   int* err) {
-  using Cf = Cfg<S, NEX, CPLX>;
+                   int* err, int group_m) {
+  using Cf = Cfg<S, NEX, CPLX, NTT>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = smem;
@@ -271,7 +276,12 @@ __global__ void __maxnreg__(168)
   // a CTA of a launch that already hit a wait limit does nothing
   if (*(volatile int*)err != 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tile = blockIdx.x, m_tile = blockIdx.y;
+  const int num_m = (M + BM - 1) / BM, num_n = (N + Cf::NCOLS - 1) / Cf::NCOLS;
+  const int per_group = group_m * num_n;
+  const int first_m = ((int)blockIdx.x / per_group) * group_m;
+  const int gm = min(group_m, num_m - first_m);
+  const int in_group = (int)blockIdx.x % per_group;
+  const int m_tile = first_m + in_group % gm, n_tile = in_group / gm;
   const int m0 = m_tile * BM, n0 = n_tile * Cf::NCOLS;
   const int nkb = (K + BK - 1) / BK;
   const int nchunks = (nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK;
@@ -838,10 +848,10 @@ void invalidate(Workspace& w) {
 
 // C(M x N) = L(M x K) R(K x N) from digit planes (left: rows = M vectors of length K, right:
 // rows = N vectors of length K), split with l_slices_total / S slices respectively.
-template <int S, int NEX, bool CPLX>
+template <int S, int NEX, bool CPLX, int NTT>
 static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double* lsc, int l_slices_total,
                    const void* rpl, const double* rsc, int64_t M, int64_t N, int64_t K, const Epi& e) {
-  using Cf = Cfg<S, NEX, CPLX>;
+  using Cf = Cfg<S, NEX, CPLX, NTT>;
   const int64_t kp = kpad(K);
   const int ap = CPLX ? 2 : 1, bp = CPLX ? 3 : 1;
   CUtensorMap ma = make_map(lpl, K, kp, M, l_slices_total * ap, BM);
@@ -850,17 +860,18 @@ static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double*
   static std::once_flag attr_once;
   cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [&]() {
-    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX, NTT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     Cf::SMEM_BYTES);
   });
   CHASE_CUDA(attr_err);
   EpiArgs ea{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
-  dim3 grid(ceil_div(N, Cf::NCOLS), ceil_div(M, BM));
-  CHASE_REQUIRE(grid.y <= 65535, 1, "split product: M too large");
+  const int64_t tiles = (int64_t)ceil_div(N, Cf::NCOLS) * (int64_t)ceil_div(M, BM);
+  CHASE_REQUIRE(tiles <= 0x7fffffff, 1, "split product: too many tiles");
+  const int group_m = std::max(1, w.group_m);
   const bool timed = w.timing && w.ev_used + 2 <= (int)w.ev.size();
   if (timed) CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used], st));
-  oz_gemm_kernel<S, NEX, CPLX><<<grid, NTHREADS, Cf::SMEM_BYTES, st>>>(ma, mb, (int)M, (int)N, (int)K, lsc, rsc, ea,
-                                                                         w.flags);
+  oz_gemm_kernel<S, NEX, CPLX, NTT><<<(unsigned)tiles, NTHREADS, Cf::SMEM_BYTES, st>>>(
+      ma, mb, (int)M, (int)N, (int)K, lsc, rsc, ea, w.flags, group_m);
   CHASE_CHECK_LAUNCH();
   if (timed) {
     CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used + 1], st));
@@ -872,10 +883,14 @@ template <bool CPLX>
 static void dispatch(cudaStream_t st, Workspace& w, int S_, const void* lpl, const double* lsc, int l_slices_total,
                      int64_t M, int64_t N, int64_t K, const Epi& e) {
   CHASE_REQUIRE(K <= 65472, 1, "split products support K <= 65472 (int64 exact-level sums)");
-  if (S_ == 7) launch<7, 5, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
-  else if (S_ == 6) launch<6, 5, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
-  else if (S_ == 3) launch<3, 0, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
-  else launch<2, 0, CPLX>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  // a narrow right operand (up to 8 complex or 16 real columns: the Lanczos block) takes the N = 16 tile, so
+  // the launch streams the left planes once without computing unused accumulator columns
+  const bool narrow = N <= (CPLX ? 8 : 16);
+  if (S_ == 7 && narrow) launch<7, 5, CPLX, 16>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  else if (S_ == 7) launch<7, 5, CPLX, 80>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  else if (S_ == 6) launch<6, 5, CPLX, 80>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  else if (S_ == 3) launch<3, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  else launch<2, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
 }
 
 template <typename T>

@@ -113,12 +113,14 @@ def test_backward_c5_gradient_check(pkg):
 
 def test_backward_c5_central_differences(pkg):
     """The n = 4096 differentiation workload checked as the gradient check is set: the GPU forward at
-    tol 1e-13 (about the FP64 floor there) and the hand-written backward, against central differences
-    (h = 1e-6) of the exact loss along 8 seeded symmetric directions, to 1e-6 relative."""
+    tol 1e-12 (1e-13 is below what FP64 residuals reach at this n) and the hand-written backward, against
+    central differences (h = 1e-6) of the exact loss along 8 seeded symmetric directions, to 1e-6
+    relative.  The forward's eigenvector error (residual over the 1e-3 gaps, about 1e-9) stays far below
+    the check's tolerance."""
     p = G.problem_c5(4096)
     A = p.dense()
     w, Bm = p.extra["w"], p.extra["B"]
-    L, gA, _ = _gpu_grad(pkg, p, A, w, Bm, tol=1e-13, minres_tol=1e-12)
+    L, gA, _ = _gpu_grad(pkg, p, A, w, Bm, tol=1e-12, minres_tol=1e-12)
     assert abs(L - _exact_loss(A, 64, w, Bm)) <= 1e-9 * abs(L)
     g = G.rng(5, 0, 9)
     h = 1e-6
