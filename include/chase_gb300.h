@@ -95,6 +95,8 @@ typedef struct {
   int rr_fallbacks;             /* Rayleigh-Ritz eigensolves that fell back to the FP64 Jacobi */
   int qr_replaced;              /* numerically dependent columns of filtered blocks that the QR step
                                    replaced by seeded random vectors */
+  int filter_reorth;            /* orthonormalisations inside equal-degree filters whose amplification
+                                   would exceed 1e7 (the filtered span is unchanged) */
 } chase_stats_t;
 
 /* Kernel launches made by this library in this process so far (all contexts). */

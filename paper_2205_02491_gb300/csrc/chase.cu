@@ -252,16 +252,67 @@ template <typename T> struct Solver {
     gemm(OP_N, L + k1 + (int64_t)k1 * ld, ld, OP_N, tmp, k2, k2, k1, k2, e2, mode);  // B = -C^-1 tmp
   }
 
+  // Y_s (n x k, ld n) <- Q with Y_s = Q R (Cholesky-QR2 with column equilibration) and Y_p <- Y_p R^{-1}:
+  // both iterates of the three-term recurrence take the same right factor, so the recurrence goes on
+  // and the filtered block keeps its span.  Returns false (both blocks rescaled consistently, otherwise
+  // as they were after the last completed pass) when a Cholesky factorisation fails.
+  bool orthonormalize_pair(T* Ys, T* Yp, int64_t n, int k) {
+    T* Gm = Gb();
+    for (int pass = 0; pass < 2; ++pass) {
+      colnorms<T>(st(), n, k, Ys, n, c->dwork);
+      scale_cols<T>(st(), n, k, Ys, n, c->dwork, 1);
+      scale_cols<T>(st(), n, k, Yp, n, c->dwork, 1);
+      Epi e;
+      e.C = Gm;
+      e.ldc = k;
+      gemm(OP_C, Ys, n, OP_N, Ys, n, k, k, n, e, CHASE_FP64);
+      hermitianize<T>(st(), k, Gm, k);
+      CHASE_CUDA(cudaMemsetAsync(c->info, 0, sizeof(int), st()));
+      potrf_lower<T>(st(), k, Gm, k, c->info, W(), c->work_elems);
+      int info = 0;
+      CHASE_CUDA(cudaMemcpyAsync(&info, c->info, sizeof(int), cudaMemcpyDeviceToHost, st()));
+      CHASE_CUDA(cudaStreamSynchronize(st()));
+      if (info != 0) return false;
+      if (use_split(CHASE_FP64, n, k, k)) {
+        zero_upper<T>(st(), k, Gm, k);
+        trtri_diag<T>(st(), k, Gm, k);
+        trtri_combine(Gm, k, k, Zb(), CHASE_FP64);
+        for (T* X : {Ys, Yp}) {
+          Epi q;
+          q.C = X;
+          q.ldc = n;
+          gemm(OP_N, X, n, OP_C, Gm, k, n, k, k, q, CHASE_FP64);
+        }
+      } else {
+        trsm_right_lh<T>(st(), n, k, Ys, n, Gm, k, W(), c->work_elems);
+        trsm_right_lh<T>(st(), n, k, Yp, n, Gm, k, W(), c->work_elems);
+      }
+    }
+    return true;
+  }
+
   // ------------------------------------------------------------ Algorithm 1, line 4
   // Filter the k columns of Y0 (ld n) in place; T1 (ld n) is the ping-pong partner.
   // deg_host non-decreasing; deg_dev the same on the device.
+  // reorth: when every column has the same degree (the first outer iteration) and the filter would
+  // amplify the component along mu_1 by more than 1e7 over the damped interval, the iterate is
+  // orthonormalised (with the previous one carried along) every s_split steps, keeping each stretch's
+  // amplification below 1e7.  In exact arithmetic the filtered span is unchanged; it keeps the block
+  // within reach of the Cholesky-QR of line 5 (a Householder QR copes with any conditioning, a
+  // Cholesky-QR only with about 1e8).
   int64_t filter(const T* A, int64_t n, int64_t lda, T* Y0, T* Y1, int k, const int* deg_host, const int* deg_dev,
-                 double b_sup, double mu_1, double mu_ne, int mode) {
+                 double b_sup, double mu_1, double mu_ne, int mode, bool reorth = false) {
     if (k <= 0) return 0;
     int mmax = deg_host[k - 1];
     double cc, ee;
     std::vector<double> al, be;
     filter_coeffs(b_sup, mu_1, mu_ne, mmax, cc, ee, al, be);
+    int s_split = mmax + 1;
+    if (reorth && k >= 2 && deg_host[0] == mmax) {
+      const double t1 = std::fabs((mu_1 - cc) / ee);
+      const double rho = t1 > 1.0 ? t1 + std::sqrt(t1 * t1 - 1.0) : 1.0;
+      if (rho > 1.0 + 1e-12) s_split = std::max(1, (int)std::floor(std::log(1e7) / std::log(rho)));
+    }
     T* B[2] = {Y0, Y1};
     int f = 0;
     int64_t mv = 0;
@@ -286,6 +337,8 @@ template <typename T> struct Solver {
       }
       hemm(A, n, lda, in, n, cols, e, mode);
       c->stats.filter_launches++;
+      if (s % s_split == 0 && s < mmax && orthonormalize_pair(B[s & 1], B[(s - 1) & 1], n, k))
+        c->stats.filter_reorth++;
     }
     dim3 grid(std::min<unsigned>(ceil_div(n, 256), 64), k);
     gather_odd_kernel<T><<<grid, 256, 0, st()>>>(n, deg_dev, Y0, n, Y1, n);
@@ -757,7 +810,7 @@ template <typename T> struct Solver {
       {
         Timer t(c, 1, &S.ms_filter);
         if (oz::available()) oz::timing_begin(c->ozw);
-        int64_t mv = filter(A, n, lda, Vact, T1act, k, m.data(), c->deg, b_sup, mu_1, mu_ne, fmode);
+        int64_t mv = filter(A, n, lda, Vact, T1act, k, m.data(), c->deg, b_sup, mu_1, mu_ne, fmode, true);
         if (oz::available()) {
           int nl = 0;
           double ms = oz::timing_collect(c->ozw, &nl);

@@ -202,6 +202,26 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// EPI_COLS consecutive accumulator columns of this thread's lane into r, without waiting: as few
+// tcgen05.ld instructions as the width allows (32-column loads, then 8-column loads)
+template <int COLS> __device__ __forceinline__ void tmem_ld_cols_nowait(uint32_t taddr, uint32_t* r) {
+#pragma unroll
+  for (int h = 0; h < COLS / 32; ++h) tmem_ld32_nowait(taddr + (uint32_t)(h * 32), &r[h * 32]);
+#pragma unroll
+  for (int h = (COLS / 32) * 4; h < COLS / 8; ++h) tmem_ld8_nowait(taddr + (uint32_t)(h * 8), &r[h * 8]);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -487,9 +507,7 @@ __global__ void __maxnreg__(168)
         for (int L = 0; L < (NEX > 0 ? NEX : 1); ++L) {
           // all columns of one level in flight, one wait
           uint32_t r[EPI_COLS];
-#pragma unroll
-          for (int h = 0; h < EPI_COLS / 8; ++h)
-            tmem_ld8_nowait(lane_addr + (uint32_t)(L * Cf::NT + wg * EPI_COLS + h * 8), &r[h * 8]);
+          tmem_ld_cols_nowait<EPI_COLS>(lane_addr + (uint32_t)(L * Cf::NT + wg * EPI_COLS), r);
           tmem_wait_ld();
           const float sc = (float)(1ull << (8 * L));  // level L unit is 2^-8L
 #pragma unroll

@@ -115,8 +115,10 @@ def test_backward_c5_central_differences(pkg):
     """The n = 4096 differentiation workload checked as the gradient check is set: the GPU forward at
     tol 1e-12 (1e-13 is below what FP64 residuals reach at this n) and the hand-written backward, against
     central differences (h = 1e-6) of the exact loss along 8 seeded symmetric directions, to 1e-6
-    relative.  The forward's eigenvector error (residual over the 1e-3 gaps, about 1e-9) stays far below
-    the check's tolerance."""
+    relative.  The directions are scaled to spectral norm about 1 (a symmetric Gaussian of this size has
+    norm sqrt(2n) = 90, and a step of 9e-5 against eigenvalue gaps of 1e-3 would make the central
+    difference's own h^2 error the largest term).  The forward's eigenvector error (residual over the
+    gaps, about 1e-9) stays far below the check's tolerance."""
     p = G.problem_c5(4096)
     A = p.dense()
     w, Bm = p.extra["w"], p.extra["B"]
@@ -126,7 +128,7 @@ def test_backward_c5_central_differences(pkg):
     h = 1e-6
     for _ in range(8):
         D = g.standard_normal(A.shape)
-        D = 0.5 * (D + D.T)
+        D = 0.5 * (D + D.T) / np.sqrt(2.0 * A.shape[0])
         fd = (_exact_loss(A + h * D, 64, w, Bm) - _exact_loss(A - h * D, 64, w, Bm)) / (2 * h)
         an = float(np.sum(gA * D))
         assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
