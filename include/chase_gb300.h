@@ -69,9 +69,10 @@ typedef struct {
   int oz_slices;       /* FP64 mode: BF16 slices per operand, 6 or 7 (default 7) */
   int native_below_mflop; /* products below this many MFLOP use DFMA kernels; 0: always
                              split tensor-core products (default 2000) */
-  int batch_workers;   /* chase_solve_batched: problems solved concurrently, each worker with its
-                          own stream and workspace sized (n_max, ne_max); 1: one after the other
-                          on the context's stream (default 1, at most 32) */
+  int batch_workers;   /* chase_solve_batched: host threads that run the per-problem stages (grouped
+                          mode), or problems solved concurrently, each worker with its own stream and
+                          workspace sized (n_max, ne_max) (worker-pool mode); default 1, at most 32 */
+  int batch_grouped;   /* chase_solve_batched: 1 (default) grouped mode, 0 worker-pool mode; see there */
 } chase_opts;
 
 typedef struct {

@@ -28,7 +28,7 @@ EXPORTED = ["chase_default_opts", "chase_create", "chase_destroy", "chase_last_e
 class Opts(C.Structure):
     _fields_ = [("maxdeg", C.c_int), ("lanczos_steps", C.c_int), ("lanczos_runs", C.c_int), ("maxiter", C.c_int),
                 ("extra_deg", C.c_int), ("nfinal", C.c_int), ("oz_slices", C.c_int),
-                ("native_below_mflop", C.c_int), ("batch_workers", C.c_int)]
+                ("native_below_mflop", C.c_int), ("batch_workers", C.c_int), ("batch_grouped", C.c_int)]
 
 
 class Stats(C.Structure):

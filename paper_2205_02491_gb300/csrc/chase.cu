@@ -83,6 +83,8 @@ struct chase_ctx {
   cudaEvent_t ev[8] = {};
   // batched solves: opts.batch_workers - 1 more contexts, each with its own stream
   std::vector<chase_ctx*> workers;
+  // grouped batched solves: one context per problem (sized to it, own stream), kept between calls
+  std::vector<chase_ctx*> slots;
 };
 
 namespace {
@@ -728,7 +730,26 @@ template <typename T> struct Solver {
   }
 
   // ------------------------------------------------------------ Algorithm 1
-  void solve(const T* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg, int mode, const T* V0,
+  // Host state of one solve between the stages of an outer iteration (a batched solve keeps one per
+  // problem and runs the stages of all problems in lockstep).
+  struct Run {
+    const T* A = nullptr;
+    int64_t n = 0, lda = 0;
+    int nev = 0, nex = 0, ne = 0, mode = 0, deg = 0;
+    double thresh = 0.0, norm_est = 0.0, b_sup = 0.0, mu_1 = 0.0, mu_ne = 0.0;
+    std::vector<int> m;  // degrees of the active columns (non-decreasing)
+    int l = 0, it = 0;
+    bool lowp = false;
+    double lowp_floor = 0.0, prev_minres = 1e308;
+    std::vector<int> degbuf;
+    std::vector<double> resbuf, reslock;
+    int k() const { return ne - l; }
+    bool done(int maxiter) const { return l >= nev || it >= maxiter; }
+    int fmode() const { return (mode == CHASE_FP64_NATIVE) ? CHASE_FP64_NATIVE : (lowp ? mode : CHASE_FP64); }
+  };
+
+  // Validation, NaN checks, Lanczos bounds (line 2), start block and initial degrees (line 1).
+  void begin(Run& R, const T* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg, int mode, const T* V0,
              const T* L0) {
     const int ne = nev + nex;
     CHASE_REQUIRE(n >= 1 && n <= c->n_max, CHASE_ERR_ARG, "n out of range for this context");
@@ -743,7 +764,6 @@ template <typename T> struct Solver {
     c->stats = chase_stats_t{};
     oz::invalidate(c->ozw);  // A may hold new values at the same address
     chase_stats_t& S = c->stats;
-    Timer ttot(c, 0, &S.ms_total);
     check_nan(A, n, (int)n, lda, "A");
     check_nan(V0, n, ne, n, "V0");
     const int runs = c->opts.lanczos_runs, steps = std::min<int>(c->opts.lanczos_steps, (int)n);
@@ -769,137 +789,180 @@ template <typename T> struct Solver {
     double hb[6];
     CHASE_CUDA(cudaMemcpyAsync(hb, c->dwork, 4 * sizeof(double), cudaMemcpyDeviceToHost, st()));
     CHASE_CUDA(cudaStreamSynchronize(st()));
-    double b_sup = hb[0], mu_1 = hb[1], mu_ne = hb[2], theta_max = hb[3];
-    S.b_sup = b_sup;
-    S.mu_1 = mu_1;
-    S.mu_ne = mu_ne;
-    double norm_est = std::max(std::fabs(mu_1), std::fabs(theta_max));
-    S.norm_est = norm_est;
-    const double thresh = tol * norm_est;
-    CHASE_REQUIRE(std::isfinite(b_sup) && std::isfinite(mu_1) && std::isfinite(mu_ne), CHASE_ERR_NAN,
+    R = Run{};
+    R.A = A;
+    R.n = n;
+    R.lda = lda;
+    R.nev = nev;
+    R.nex = nex;
+    R.ne = ne;
+    R.mode = mode;
+    R.deg = deg;
+    R.b_sup = hb[0];
+    R.mu_1 = hb[1];
+    R.mu_ne = hb[2];
+    const double theta_max = hb[3];
+    S.b_sup = R.b_sup;
+    S.mu_1 = R.mu_1;
+    S.mu_ne = R.mu_ne;
+    R.norm_est = std::max(std::fabs(R.mu_1), std::fabs(theta_max));
+    S.norm_est = R.norm_est;
+    R.thresh = tol * R.norm_est;
+    CHASE_REQUIRE(std::isfinite(R.b_sup) && std::isfinite(R.mu_1) && std::isfinite(R.mu_ne), CHASE_ERR_NAN,
                   "non-finite Lanczos bounds");
-
     copy_cols<T>(st(), n, ne, V0, n, V(), n);
-    std::vector<int> m(ne, deg);
+    R.m.assign(ne, deg);
     fill_int_kernel<<<ceil_div(ne, 256), 256, 0, st()>>>(ne, c->deg, deg);
     CHASE_CHECK_LAUNCH();
-    int l = 0;
-    // mixed-precision policy: bulk filter in the low-precision mode until the smallest unconverged
-    // relative residual reaches its floor, then FP64 for the remaining iterations.
-    // mixed modes: bulk filter in split-BF16 while it still makes progress; switch to FP64 for
-    // the rest once the smallest unconverged relative residual reaches the bulk precision floor
-    // or stops falling by at least a factor 4 per iteration
-    bool lowp = (mode == CHASE_BF16x3 || mode == CHASE_BF16x6);
-    const double lowp_floor = (mode == CHASE_BF16x3) ? 1e-3 : 3e-5;
-    double prev_minres = 1e308;
-    int it = 0;
-    struct {
-      int lock;
-      int pad;
-      double bnd[6];
-    } hstat;
-    std::vector<int> degbuf(ne);
-    std::vector<double> resbuf(ne), reslock(ne);
-    while (l < nev && it < c->opts.maxiter) {
-      ++it;
-      const int k = ne - l;
-      T* Vact = V() + (int64_t)l * n;
-      T* T1act = T1() + (int64_t)l * n;
-      T* T2act = T2() + (int64_t)l * n;
-      int fmode = (mode == CHASE_FP64_NATIVE) ? CHASE_FP64_NATIVE : (lowp ? mode : CHASE_FP64);
-      {
-        Timer t(c, 1, &S.ms_filter);
-        if (oz::available()) oz::timing_begin(c->ozw);
-        int64_t mv = filter(A, n, lda, Vact, T1act, k, m.data(), c->deg, b_sup, mu_1, mu_ne, fmode, true);
-        if (oz::available()) {
-          int nl = 0;
-          double ms = oz::timing_collect(c->ozw, &nl);
-          if (lowp) {
-            S.ms_filter_kernel_lowp += ms;
-          } else {
-            S.ms_filter_kernel += ms;
-            S.filter_kernel_launches += nl;
-          }
-        }
-        S.matvecs += mv;
-        if (lowp) {
-          S.matvecs_lowp += mv;
-          S.lowp_iterations++;
-        }
-        t.stop();
-      }
-      {
-        Timer t(c, 1, &S.ms_qr);
-        qr(V(), n, l, Vact, n, n, k, mode == CHASE_FP64_NATIVE ? CHASE_FP64_NATIVE : CHASE_FP64);
-        t.stop();
-      }
-      {
-        Timer t(c, 1, &S.ms_rr);
-        rayleigh_ritz(A, n, lda, Vact, T2act, T1act, k, c->ritz, c->res, fmode);
-        t.stop();
-      }
-      {
-        Timer t(c, 1, &S.ms_resid);
-        bookkeeping(st(), k, c->ritz, c->res, thresh, b_sup, c->bounds, c->opts.maxdeg, c->opts.extra_deg,
-                    c->status_dev, c->deg, c->perm, c->ritz2, c->res2, c->iwork);
-        CHASE_CUDA(cudaMemcpyAsync(&hstat.lock, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st()));
-        CHASE_CUDA(cudaMemcpyAsync(hstat.bnd, c->bounds, 6 * sizeof(double), cudaMemcpyDeviceToHost, st()));
-        CHASE_CUDA(cudaMemcpyAsync(degbuf.data(), c->deg, k * sizeof(int), cudaMemcpyDeviceToHost, st()));
-        CHASE_CUDA(cudaMemcpyAsync(resbuf.data(), c->res2, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
-        CHASE_CUDA(cudaMemcpyAsync(reslock.data(), c->res, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
-        CHASE_CUDA(cudaStreamSynchronize(st()));
-        CHASE_REQUIRE(oz::read_flags(st(), c->ozw) == 0, CHASE_ERR_TIMEOUT, "a tensor-core product hit its wait limit");
-        const int p = hstat.lock;
-        for (int a = 0; a < p; ++a) S.max_resid = std::max(S.max_resid, reslock[a] / norm_est);
-        // lock: Ritz values of the converged prefix, then reorder the remaining active columns
-        if (p > 0) CHASE_CUDA(cudaMemcpyAsync(c->lam_locked + l, c->ritz, p * sizeof(double), cudaMemcpyDeviceToDevice, st()));
-        const int kr = k - p;
-        if (kr > 0) {
-          permute_cols<T>(st(), n, kr, Vact, n, T1act, n, c->perm);
-          copy_cols<T>(st(), n, kr, T1act, n, Vact + (int64_t)p * n, n);
-        }
-        // the device degree array must follow the new active block (it starts at l + p)
-        l += p;
-        mu_1 = hstat.bnd[1];
-        mu_ne = hstat.bnd[2];
-        m.assign(degbuf.begin(), degbuf.begin() + kr);
-        if (verbose()) {
-          double mr = 0.0, mn = 1e308;
-          for (int a = 0; a < kr; ++a) {
-            mr = std::max(mr, resbuf[a] / norm_est);
-            mn = std::min(mn, resbuf[a] / norm_est);
-          }
-          fprintf(stderr, "[chase] it=%d mode=%d k=%d locked=%d(+%d) mu1=%.6g mune=%.6g res[min,max]=%.3e,%.3e deg[0,last]=%d,%d fallbacks=%d ms[filter,qr,rr,resid]=%.1f,%.1f,%.1f,%.1f\n",
-                  it, fmode, k, l, p, mu_1, mu_ne, mn, mr, kr ? m[0] : 0, kr ? m[kr - 1] : 0, S.qr_fallbacks,
-                  S.ms_filter, S.ms_qr, S.ms_rr, S.ms_resid);
-        }
-        if (lowp) {
-          double minres = 1e308;
-          for (int a = 0; a < kr; ++a) minres = std::min(minres, resbuf[a] / norm_est);
-          if (kr == 0 || minres <= lowp_floor || minres > 0.25 * prev_minres ||
-              it >= c->opts.maxiter - c->opts.nfinal)
-            lowp = false;
-          prev_minres = minres;
-        }
-        t.stop();
+    // mixed modes: bulk filter in split-BF16 while it still makes progress; switch to FP64 for the rest
+    // once the smallest unconverged relative residual reaches the bulk precision floor or stops falling
+    // by at least a factor 4 per iteration
+    R.lowp = (mode == CHASE_BF16x3 || mode == CHASE_BF16x6);
+    R.lowp_floor = (mode == CHASE_BF16x3) ? 1e-3 : 3e-5;
+    R.degbuf.assign(ne, 0);
+    R.resbuf.assign(ne, 0.0);
+    R.reslock.assign(ne, 0.0);
+  }
+
+  // Line 4 of one outer iteration (the filter of the active block), timed.
+  void filter_stage(Run& R) {
+    chase_stats_t& S = c->stats;
+    const int k = R.k();
+    T* Vact = V() + (int64_t)R.l * R.n;
+    T* T1act = T1() + (int64_t)R.l * R.n;
+    Timer t(c, 1, &S.ms_filter);
+    if (oz::available()) oz::timing_begin(c->ozw);
+    int64_t mv = filter(R.A, R.n, R.lda, Vact, T1act, k, R.m.data(), c->deg, R.b_sup, R.mu_1, R.mu_ne, R.fmode(), true);
+    if (oz::available()) {
+      int nl = 0;
+      double ms = oz::timing_collect(c->ozw, &nl);
+      if (R.lowp) {
+        S.ms_filter_kernel_lowp += ms;
+      } else {
+        S.ms_filter_kernel += ms;
+        S.filter_kernel_launches += nl;
       }
     }
-    S.iterations = it;
-    S.locked = l;
-    CHASE_REQUIRE(l >= nev, CHASE_ERR_NOCONV, "maxiter reached before nev pairs converged");
-    // final order: nev smallest locked values ascending
-    final_sort_kernel<<<ceil_div(l, 128), 128, 0, st()>>>(l, nev, c->lam_locked, c->eigvals, c->lam_sorted, c->perm);
+    count_matvecs(R, mv);
+    t.stop();
+  }
+
+  void count_matvecs(Run& R, int64_t mv) {
+    chase_stats_t& S = c->stats;
+    S.matvecs += mv;
+    if (R.lowp) {
+      S.matvecs_lowp += mv;
+      S.lowp_iterations++;
+    }
+  }
+
+  // Lines 5-14 of one outer iteration: QR, Rayleigh-Ritz, residuals, locking, bounds, degrees, sort.
+  void after_filter(Run& R) {
+    chase_stats_t& S = c->stats;
+    const int64_t n = R.n;
+    const int k = R.k();
+    T* Vact = V() + (int64_t)R.l * n;
+    T* T1act = T1() + (int64_t)R.l * n;
+    T* T2act = T2() + (int64_t)R.l * n;
+    const int fmode = R.fmode();
+    {
+      Timer t(c, 1, &S.ms_qr);
+      qr(V(), n, R.l, Vact, n, n, k, R.mode == CHASE_FP64_NATIVE ? CHASE_FP64_NATIVE : CHASE_FP64);
+      t.stop();
+    }
+    {
+      Timer t(c, 1, &S.ms_rr);
+      rayleigh_ritz(R.A, n, R.lda, Vact, T2act, T1act, k, c->ritz, c->res, fmode);
+      t.stop();
+    }
+    {
+      Timer t(c, 1, &S.ms_resid);
+      struct {
+        int lock;
+        int pad;
+        double bnd[6];
+      } hstat;
+      bookkeeping(st(), k, c->ritz, c->res, R.thresh, R.b_sup, c->bounds, c->opts.maxdeg, c->opts.extra_deg,
+                  c->status_dev, c->deg, c->perm, c->ritz2, c->res2, c->iwork);
+      CHASE_CUDA(cudaMemcpyAsync(&hstat.lock, c->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st()));
+      CHASE_CUDA(cudaMemcpyAsync(hstat.bnd, c->bounds, 6 * sizeof(double), cudaMemcpyDeviceToHost, st()));
+      CHASE_CUDA(cudaMemcpyAsync(R.degbuf.data(), c->deg, k * sizeof(int), cudaMemcpyDeviceToHost, st()));
+      CHASE_CUDA(cudaMemcpyAsync(R.resbuf.data(), c->res2, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
+      CHASE_CUDA(cudaMemcpyAsync(R.reslock.data(), c->res, k * sizeof(double), cudaMemcpyDeviceToHost, st()));
+      CHASE_CUDA(cudaStreamSynchronize(st()));
+      CHASE_REQUIRE(oz::read_flags(st(), c->ozw) == 0, CHASE_ERR_TIMEOUT, "a tensor-core product hit its wait limit");
+      const int p = hstat.lock;
+      for (int a = 0; a < p; ++a) S.max_resid = std::max(S.max_resid, R.reslock[a] / R.norm_est);
+      // lock: Ritz values of the converged prefix, then reorder the remaining active columns
+      if (p > 0)
+        CHASE_CUDA(cudaMemcpyAsync(c->lam_locked + R.l, c->ritz, p * sizeof(double), cudaMemcpyDeviceToDevice, st()));
+      const int kr = k - p;
+      if (kr > 0) {
+        permute_cols<T>(st(), n, kr, Vact, n, T1act, n, c->perm);
+        copy_cols<T>(st(), n, kr, T1act, n, Vact + (int64_t)p * n, n);
+      }
+      // the device degree array must follow the new active block (it starts at l + p)
+      R.l += p;
+      R.mu_1 = hstat.bnd[1];
+      R.mu_ne = hstat.bnd[2];
+      R.m.assign(R.degbuf.begin(), R.degbuf.begin() + kr);
+      if (verbose()) {
+        double mr = 0.0, mn = 1e308;
+        for (int a = 0; a < kr; ++a) {
+          mr = std::max(mr, R.resbuf[a] / R.norm_est);
+          mn = std::min(mn, R.resbuf[a] / R.norm_est);
+        }
+        fprintf(stderr, "[chase] it=%d mode=%d k=%d locked=%d(+%d) mu1=%.6g mune=%.6g res[min,max]=%.3e,%.3e deg[0,last]=%d,%d fallbacks=%d ms[filter,qr,rr,resid]=%.1f,%.1f,%.1f,%.1f\n",
+                R.it, fmode, k, R.l, p, R.mu_1, R.mu_ne, mn, mr, kr ? R.m[0] : 0, kr ? R.m[kr - 1] : 0, S.qr_fallbacks,
+                S.ms_filter, S.ms_qr, S.ms_rr, S.ms_resid);
+      }
+      if (R.lowp) {
+        double minres = 1e308;
+        for (int a = 0; a < kr; ++a) minres = std::min(minres, R.resbuf[a] / R.norm_est);
+        if (kr == 0 || minres <= R.lowp_floor || minres > 0.25 * R.prev_minres ||
+            R.it >= c->opts.maxiter - c->opts.nfinal)
+          R.lowp = false;
+        R.prev_minres = minres;
+      }
+      t.stop();
+    }
+  }
+
+  // Result of the solve: NOCONV check, the nev smallest locked pairs ascending, warm-start block.
+  void finish(Run& R) {
+    chase_stats_t& S = c->stats;
+    const int64_t n = R.n;
+    S.iterations = R.it;
+    S.locked = R.l;
+    CHASE_REQUIRE(R.l >= R.nev, CHASE_ERR_NOCONV, "maxiter reached before nev pairs converged");
+    final_sort_kernel<<<ceil_div(R.l, 128), 128, 0, st()>>>(R.l, R.nev, c->lam_locked, c->eigvals, c->lam_sorted, c->perm);
     CHASE_CHECK_LAUNCH();
     // T1 = [locked pairs ascending | remaining active block]: the first nev columns are the
     // eigenvectors, the whole block is a warm start for a nearby problem
-    permute_cols<T>(st(), n, l, V(), n, T1(), n, c->perm);
-    if (ne > l) copy_cols<T>(st(), n, ne - l, V() + (int64_t)l * n, n, T1() + (int64_t)l * n, n);
+    permute_cols<T>(st(), n, R.l, V(), n, T1(), n, c->perm);
+    if (R.ne > R.l) copy_cols<T>(st(), n, R.ne - R.l, V() + (int64_t)R.l * n, n, T1() + (int64_t)R.l * n, n);
     c->n = n;
-    c->nev = nev;
-    c->nex = nex;
-    c->l_final = l;
+    c->nev = R.nev;
+    c->nex = R.nex;
+    c->l_final = R.l;
     c->have_result = true;
+  }
+
+  void solve(const T* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg, int mode, const T* V0,
+             const T* L0) {
+    Run R;
+    c->stats = chase_stats_t{};
+    Timer ttot(c, 0, &c->stats.ms_total);
+    begin(R, A, n, lda, nev, nex, tol, deg, mode, V0, L0);
+    while (!R.done(c->opts.maxiter)) {
+      ++R.it;
+      filter_stage(R);
+      after_filter(R);
+    }
+    // on NOCONV the timers still record: finish() throws after the iteration count is stored
+    c->stats.ms_total = 0.0;
     ttot.stop();
+    finish(R);
   }
 };
 
@@ -976,6 +1039,7 @@ void chase_default_opts(chase_opts* o) {
   o->oz_slices = 7;
   o->native_below_mflop = 2000;
   o->batch_workers = 1;
+  o->batch_grouped = 1;
 }
 
 static int64_t lanczos_elems(int64_t n, int runs, int steps) {
@@ -1013,7 +1077,8 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
   if (opts) c->opts = *opts;
   if (c->opts.maxdeg < 1 || c->opts.lanczos_runs < 1 || c->opts.lanczos_runs > 8 || c->opts.lanczos_steps < 1 ||
       c->opts.lanczos_steps > 64 || c->opts.maxiter < 1 || c->opts.oz_slices < 6 || c->opts.oz_slices > 7 ||
-      c->opts.native_below_mflop < 0 || c->opts.batch_workers < 1 || c->opts.batch_workers > 32) {
+      c->opts.native_below_mflop < 0 || c->opts.batch_workers < 1 || c->opts.batch_workers > 32 ||
+      c->opts.batch_grouped < 0 || c->opts.batch_grouped > 1) {
     delete c;
     return CHASE_ERR_ARG;
   }
@@ -1029,7 +1094,8 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
     for (auto& e : c->ev) CHASE_CUDA(cudaEventCreate(&e));
     size_t freeb = 0, totb = 0;
     CHASE_CUDA(cudaMemGetInfo(&freeb, &totb));
-    int64_t need = chase_workspace_bytes(n_max, ne_max, dtype, &c->opts) * (int64_t)c->opts.batch_workers;
+    const int nctx = c->opts.batch_grouped ? 1 : c->opts.batch_workers;
+    int64_t need = chase_workspace_bytes(n_max, ne_max, dtype, &c->opts) * (int64_t)nctx;
     if ((size_t)need + (64ull << 20) > freeb) {
       c->err = "workspace of " + std::to_string(need) + " bytes does not fit in free device memory";
       chase_destroy(c);
@@ -1063,7 +1129,7 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
     // workers of batched solves: same sizes and options, one non-blocking stream each
     chase_opts wo = c->opts;
     wo.batch_workers = 1;
-    for (int w = 1; w < c->opts.batch_workers; ++w) {
+    for (int w = 1; w < nctx; ++w) {
       cudaStream_t ws = nullptr;
       CHASE_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
       chase_ctx* wc = nullptr;
@@ -1087,6 +1153,8 @@ void chase_destroy(chase_ctx* c) {
   if (!c) return;
   for (chase_ctx* w : c->workers) chase_destroy(w);
   c->workers.clear();
+  for (chase_ctx* w : c->slots) chase_destroy(w);
+  c->slots.clear();
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
@@ -1325,12 +1393,281 @@ static void solve_one_of_batch(chase_ctx* c, const void* A, int64_t n, int nev, 
   if (stats) *stats = c->stats;
 }
 
+}  // extern "C"
+
+// Runs fn(i) for i in [0, count) on up to `threads` host threads (each with the context's device
+// current); the first exception is rethrown after every thread has finished.
+template <typename Fn> static void parallel_for(int device, int threads, int count, Fn fn) {
+  std::atomic<int> next{0};
+  std::mutex mu;
+  int err_status = CHASE_OK;
+  std::string err_msg;
+  auto run = [&]() {
+    if (cudaSetDevice(device) != cudaSuccess) {
+      std::lock_guard<std::mutex> lock(mu);
+      if (err_status == CHASE_OK) {
+        err_status = CHASE_ERR_CUDA;
+        err_msg = "cudaSetDevice failed in a batch thread";
+      }
+      return;
+    }
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) return;
+      try {
+        fn(i);
+      } catch (const chase::Error& e) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (err_status == CHASE_OK) {
+          err_status = e.status;
+          err_msg = e.msg;
+        }
+      } catch (const std::exception& e) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (err_status == CHASE_OK) {
+          err_status = CHASE_ERR_CUDA;
+          err_msg = e.what();
+        }
+      }
+    }
+  };
+  const int nt = std::max(1, std::min(threads, count));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(run);
+  run();
+  for (auto& t : pool) t.join();
+  CHASE_REQUIRE(err_status == CHASE_OK, err_status, err_msg);
+}
+
+// Grouped batched solve: every problem runs Algorithm 1 in its own context (sized to it, own stream),
+// and the problems advance in lockstep by outer iteration.  The filter (line 4) of all problems is one
+// grouped split-product launch per degree step over every problem's tiles (a device-side list of
+// (problem, tile) blocks in the launch's parameter block) on the batch context's stream; the other
+// stages (Lanczos, QR, Rayleigh-Ritz, residuals, locking, degrees) run per problem on its stream, on
+// opts.batch_workers host threads.
+template <typename T>
+static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A, const int64_t* n, const int* nev,
+                                  const int* nex, double tol, int deg, int mode, void* const* Vd, const void* const* L0,
+                                  double* const* eigvals, chase_stats_t* stats_host) {
+  constexpr bool CPLX = S<T>::cplx;
+  // per-problem contexts, created on first use and kept while they are large enough
+  chase_opts so = c->opts;
+  so.batch_workers = 1;
+  so.batch_grouped = 0;
+  if ((int)c->slots.size() < nprob) c->slots.resize(nprob, nullptr);
+  for (int p = 0; p < nprob; ++p) {
+    chase_ctx*& sl = c->slots[p];
+    const int ne = nev[p] + nex[p];
+    if (sl && (sl->n_max < n[p] || sl->ne_max < ne)) {
+      chase_destroy(sl);
+      sl = nullptr;
+    }
+    if (!sl) {
+      cudaStream_t ws = nullptr;
+      CHASE_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+      chase_status st = chase_create(&sl, n[p], ne, c->dtype, &so, ws);
+      if (st != CHASE_OK) {
+        cudaStreamDestroy(ws);
+        sl = nullptr;
+        throw chase::Error{(int)st, "creating the workspace of batch problem " + std::to_string(p) + " failed"};
+      }
+      sl->own_stream = true;
+    }
+  }
+  // inputs the caller enqueued on the batch context's stream must be complete before the problem streams
+  CHASE_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<typename Solver<T>::Run> R(nprob);
+  std::vector<char> failed(nprob, 0);
+  int err_status = CHASE_OK;
+  std::string err_msg;
+  auto fail_problem = [&](int p, const chase::Error& e) {
+    failed[p] = 1;
+    if (err_status == CHASE_OK) {
+      err_status = e.status;
+      err_msg = "problem " + std::to_string(p) + ": " + e.msg;
+    }
+  };
+  const int threads = c->opts.batch_workers;
+  // Lanczos bounds, start blocks, initial degrees
+  {
+    std::mutex mu;
+    parallel_for(c->device, threads, nprob, [&](int p) {
+      try {
+        Solver<T>(c->slots[p]).begin(R[p], (const T*)A[p], n[p], n[p], nev[p], nex[p], tol, deg, mode, (const T*)Vd[p],
+                                     (const T*)L0[p]);
+      } catch (const chase::Error& e) {
+        std::lock_guard<std::mutex> lock(mu);
+        fail_problem(p, e);
+      }
+    });
+  }
+  c->stats = chase_stats_t{};
+  oz::invalidate(c->ozw);
+  std::vector<cudaEvent_t> evs;
+  auto event = [&]() {
+    cudaEvent_t e = nullptr;
+    CHASE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    evs.push_back(e);
+    return e;
+  };
+  struct FilterPlan {
+    int p;
+    double cc;
+    std::vector<double> al, be;
+    int f = 0;
+    int64_t mv = 0;
+  };
+  try {
+    for (int it = 0; it < c->opts.maxiter; ++it) {
+      std::vector<int> active;
+      for (int p = 0; p < nprob; ++p)
+        if (!failed[p] && !R[p].done(c->opts.maxiter)) active.push_back(p);
+      if (active.empty()) break;
+      // ---- line 4 for every active problem: one grouped launch per degree step (per arithmetic)
+      Timer tf(c, 1, &c->stats.ms_filter);
+      std::vector<FilterPlan> plans;
+      int smax = 0;
+      for (int p : active) {
+        chase_ctx* sc = c->slots[p];
+        ++R[p].it;
+        cudaEvent_t e = event();
+        CHASE_CUDA(cudaEventRecord(e, sc->stream));
+        CHASE_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
+        if (R[p].k() <= 0) continue;
+        FilterPlan fp;
+        fp.p = p;
+        double ee;
+        const int mmax = R[p].m[R[p].k() - 1];
+        filter_coeffs(R[p].b_sup, R[p].mu_1, R[p].mu_ne, mmax, fp.cc, ee, fp.al, fp.be);
+        // the digit planes of A: computed once per solve (cached in the problem's workspace)
+        oz::prepare_A<T>(c->stream, sc->ozw, R[p].A, R[p].n, R[p].lda, CHASE_FP64);
+        smax = std::max(smax, mmax);
+        plans.push_back(std::move(fp));
+      }
+      oz::timing_begin(c->ozw);
+      std::vector<oz::ProductOp> ops_hi, ops_lo;
+      for (int sstep = 1; sstep <= smax; ++sstep) {
+        ops_hi.clear();
+        ops_lo.clear();
+        for (FilterPlan& fp : plans) {
+          const int p = fp.p;
+          auto& r = R[p];
+          chase_ctx* sc = c->slots[p];
+          const int k = r.k();
+          while (fp.f < k && r.m[fp.f] < sstep) ++fp.f;
+          const int cols = k - fp.f;
+          if (cols <= 0) continue;
+          fp.mv += cols;
+          T* Vact = (T*)sc->V + (int64_t)r.l * r.n;
+          T* T1act = (T*)sc->T1 + (int64_t)r.l * r.n;
+          T* Bb[2] = {Vact, T1act};
+          T* out = Bb[sstep & 1] + (int64_t)fp.f * r.n;
+          const T* in = Bb[(sstep - 1) & 1] + (int64_t)fp.f * r.n;
+          const int fmode = r.fmode();
+          oz::split_right<T>(c->stream, sc->ozw, fmode, in, r.n, cols, r.n);
+          Epi e;
+          e.C = out;
+          e.ldc = r.n;
+          e.alpha = fp.al[sstep];
+          e.Y = in;
+          e.ldy = r.n;
+          e.gamma = -fp.al[sstep] * fp.cc;
+          if (sstep >= 2) {
+            e.Z = out;
+            e.ldz = r.n;
+            e.beta = fp.be[sstep];
+          }
+          oz::ProductOp op{sc->ozw.a_planes, sc->ozw.a_scale, sc->ozw.slices, sc->ozw.b_planes, sc->ozw.b_scale,
+                           r.n, cols, r.n, e, c->ozw.group_m};
+          (fmode == CHASE_FP64 ? ops_hi : ops_lo).push_back(op);
+          sc->stats.filter_launches++;
+        }
+        if (!ops_hi.empty()) oz::launch_group<CPLX>(c->stream, c->ozw, CHASE_FP64, ops_hi.data(), (int)ops_hi.size());
+        if (!ops_lo.empty()) {
+          // the low-precision problems of one batch share its mode
+          oz::launch_group<CPLX>(c->stream, c->ozw, mode, ops_lo.data(), (int)ops_lo.size());
+        }
+      }
+      for (FilterPlan& fp : plans) {
+        auto& r = R[fp.p];
+        chase_ctx* sc = c->slots[fp.p];
+        const int k = r.k();
+        T* Vact = (T*)sc->V + (int64_t)r.l * r.n;
+        T* T1act = (T*)sc->T1 + (int64_t)r.l * r.n;
+        dim3 grid(std::min<unsigned>(ceil_div(r.n, 256), 64), k);
+        gather_odd_kernel<T><<<grid, 256, 0, c->stream>>>(r.n, sc->deg, Vact, r.n, T1act, r.n);
+        CHASE_CHECK_LAUNCH();
+        Solver<T>(sc).count_matvecs(r, fp.mv);
+      }
+      cudaEvent_t done_f = event();
+      CHASE_CUDA(cudaEventRecord(done_f, c->stream));
+      for (int p : active) CHASE_CUDA(cudaStreamWaitEvent(c->slots[p]->stream, done_f, 0));
+      {
+        int nl = 0;
+        const double ms = oz::timing_collect(c->ozw, &nl);
+        c->stats.ms_filter_kernel += ms;
+        c->stats.filter_kernel_launches += nl;
+      }
+      tf.stop();
+      CHASE_REQUIRE(oz::read_flags(c->stream, c->ozw) == 0, CHASE_ERR_TIMEOUT,
+                    "a grouped tensor-core product hit its wait limit");
+      // ---- lines 5-14 per problem
+      std::mutex mu;
+      parallel_for(c->device, threads, (int)active.size(), [&](int i) {
+        const int p = active[i];
+        try {
+          Solver<T>(c->slots[p]).after_filter(R[p]);
+        } catch (const chase::Error& e) {
+          std::lock_guard<std::mutex> lock(mu);
+          fail_problem(p, e);
+        }
+      });
+      for (cudaEvent_t e : evs) cudaEventDestroy(e);
+      evs.clear();
+    }
+  } catch (...) {
+    for (cudaEvent_t e : evs) cudaEventDestroy(e);
+    throw;
+  }
+  // results: eigenvalues, eigenvectors followed by the rest of the search block (next start block)
+  {
+    std::mutex mu;
+    parallel_for(c->device, threads, nprob, [&](int p) {
+      if (failed[p]) return;
+      chase_ctx* sc = c->slots[p];
+      try {
+        Solver<T>(sc).finish(R[p]);
+        const int ne = nev[p] + nex[p];
+        copy_cols<T>(sc->stream, n[p], ne, (const T*)sc->T1, n[p], (T*)Vd[p], n[p]);
+        CHASE_CUDA(cudaMemcpyAsync(eigvals[p], sc->eigvals, nev[p] * sizeof(double), cudaMemcpyDeviceToDevice,
+                                   sc->stream));
+        CHASE_CUDA(cudaStreamSynchronize(sc->stream));
+      } catch (const chase::Error& e) {
+        std::lock_guard<std::mutex> lock(mu);
+        fail_problem(p, e);
+      }
+      if (stats_host) stats_host[p] = sc->stats;
+    });
+  }
+  CHASE_REQUIRE(err_status == CHASE_OK, err_status, err_msg);
+}
+
+extern "C" {
+
 chase_status chase_solve_batched(chase_ctx* c, int nprob, const void* const* A, const int64_t* n, const int* nev,
                                  const int* nex, double tol, int deg, int mode, void* const* Vd, const void* const* L0,
                                  double* const* eigvals, chase_stats_t* stats_host) {
   API_BEGIN(c)
   CHASE_REQUIRE(nprob >= 0 && A && n && nev && nex && Vd && L0 && eigvals, CHASE_ERR_ARG, "bad args");
-  if (c->workers.empty()) {
+  for (int p = 0; p < nprob; ++p)
+    CHASE_REQUIRE(n[p] >= 1 && n[p] <= c->n_max && nev[p] >= 1 && nex[p] >= 0 && nev[p] + nex[p] <= c->ne_max,
+                  CHASE_ERR_ARG, "problem " + std::to_string(p) + " exceeds the context's sizes");
+  if (c->opts.batch_grouped && mode != CHASE_FP64_NATIVE && oz::available()) {
+    if (c->dtype == CHASE_C128)
+      solve_batched_grouped<double2>(c, nprob, A, n, nev, nex, tol, deg, mode, Vd, L0, eigvals, stats_host);
+    else
+      solve_batched_grouped<double>(c, nprob, A, n, nev, nex, tol, deg, mode, Vd, L0, eigvals, stats_host);
+  } else if (c->workers.empty()) {
     for (int p = 0; p < nprob; ++p)
       solve_one_of_batch(c, A[p], n[p], nev[p], nex[p], tol, deg, mode, Vd[p], L0[p], eigvals[p],
                          stats_host ? &stats_host[p] : nullptr);

@@ -34,6 +34,19 @@ struct Workspace {
   int64_t a_n = 0;
 };
 
+// One product C = L R of a grouped launch: digit planes and scales of both operands, sizes, epilogue and
+// the tile-order group size.
+struct ProductOp {
+  const void* lpl;
+  const double* lsc;
+  int l_slices_total;
+  const void* rpl;
+  const double* rsc;
+  int64_t M, N, K;
+  Epi e;
+  int group_m;
+};
+
 bool available();
 int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices);
 void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices);
@@ -43,6 +56,12 @@ void invalidate(Workspace& w);
 void timing_begin(Workspace& w);
 double timing_collect(Workspace& w, int* launches);
 int read_flags(cudaStream_t st, Workspace& w);
+// digit planes of the right operand B (n x k, ld ldb) into w's right-operand buffer, for the given mode
+template <typename T>
+void split_right(cudaStream_t st, Workspace& w, int mode, const T* B, int64_t ldb, int k, int64_t n);
+// one launch (per 64 products) over the tiles of all the products; w supplies the error flags and timing.
+// Every op's planes must have been split with the mode's slice count (left: at least that many slices).
+template <bool CPLX> void launch_group(cudaStream_t st, Workspace& w, int mode, const ProductOp* ops, int nops);
 template <typename T>
 void prepare_A(cudaStream_t st, Workspace& w, const T* A, int64_t n, int64_t lda, int mode);
 template <typename T>

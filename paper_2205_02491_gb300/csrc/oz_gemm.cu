@@ -267,16 +267,40 @@ struct EpiArgs {
 // slices of the left operand in processing order: descending, so that the
 // first MMAs of every k-block go to the inexact accumulator while the epilogue
 // flushes the exact ones
-// Tiles run in groups of group_m row blocks: inside a group the row block varies fastest, so the CTAs that
-// are resident together share the right-operand column blocks (read from DRAM about once per group) and
-// a few left-operand row blocks, instead of every row block re-streaming all right-operand planes.
-template <int S, int NEX, bool CPLX, int NTT>
+// Parameters of one launch: G independent products (problems) C_p = L_p R_p, each with its own tensor maps,
+// sizes, scales and epilogue.  The launch's tiles are the problems' tiles back to back: problem p owns
+// blocks [tile_begin[p], tile_begin[p + 1]).  Passed as one __grid_constant__ parameter (the tensor maps
+// must live in parameter, constant or global memory for TMA); G = 64 is about 24 KB.
+template <int G> struct GroupParams {
+  CUtensorMap tmA[G];
+  CUtensorMap tmB[G];
+  EpiArgs ep[G];
+  const double* a_scale[G];
+  const double* b_scale[G];
+  int M[G], N[G], K[G], group_m[G];
+  int tile_begin[G + 1];
+  int nprob;
+};
+
+// Tiles of one problem run in groups of group_m row blocks: inside a group the row block varies fastest,
+// so the CTAs that are resident together share the right-operand column blocks (read from DRAM about
+// once per group) and a few left-operand row blocks, instead of every row block re-streaming all
+// right-operand planes.
+template <int S, int NEX, bool CPLX, int NTT, int G>
 // 168 registers: ten warps put three on some SM sub-partitions (16384 registers each)
-__global__ void __maxnreg__(168)
-    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                   int K, const double* __restrict__ a_scale, const double* __restrict__ b_scale, EpiArgs ep,
-                   int* err, int group_m) {
+__global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupParams<G> gp, int* err) {
   using Cf = Cfg<S, NEX, CPLX, NTT>;
+  // this block's problem (a short scan of the parameter block's tile offsets)
+  int prob = 0;
+  if (G > 1)
+    while (prob + 1 < gp.nprob && (int)blockIdx.x >= gp.tile_begin[prob + 1]) ++prob;
+  const CUtensorMap& tmA = gp.tmA[prob];
+  const CUtensorMap& tmB = gp.tmB[prob];
+  const EpiArgs& ep = gp.ep[prob];
+  const double* __restrict__ a_scale = gp.a_scale[prob];
+  const double* __restrict__ b_scale = gp.b_scale[prob];
+  const int M = gp.M[prob], N = gp.N[prob], K = gp.K[prob], group_m = gp.group_m[prob];
+  const int local_tile = (int)blockIdx.x - gp.tile_begin[prob];
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = smem;
@@ -298,9 +322,9 @@ __global__ void __maxnreg__(168)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_m = (M + BM - 1) / BM, num_n = (N + Cf::NCOLS - 1) / Cf::NCOLS;
   const int per_group = group_m * num_n;
-  const int first_m = ((int)blockIdx.x / per_group) * group_m;
+  const int first_m = (local_tile / per_group) * group_m;
   const int gm = min(group_m, num_m - first_m);
-  const int in_group = (int)blockIdx.x % per_group;
+  const int in_group = local_tile % per_group;
   const int m_tile = first_m + in_group % gm, n_tile = in_group / gm;
   const int m0 = m_tile * BM, n0 = n_tile * Cf::NCOLS;
   const int nkb = (K + BK - 1) / BK;
@@ -866,35 +890,60 @@ void invalidate(Workspace& w) {
 
 // C(M x N) = L(M x K) R(K x N) from digit planes (left: rows = M vectors of length K, right:
 // rows = N vectors of length K), split with l_slices_total / S slices respectively.
-template <int S, int NEX, bool CPLX, int NTT>
-static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double* lsc, int l_slices_total,
-                   const void* rpl, const double* rsc, int64_t M, int64_t N, int64_t K, const Epi& e) {
+// Products of one launch: up to G of them, each C = L R from its digit planes (left: rows = M vectors of
+// length K, split into l_slices_total slices of which the first S are used; right: rows = N vectors of
+// length K, S slices).
+template <int S, int NEX, bool CPLX, int NTT, int G>
+static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int nops) {
   using Cf = Cfg<S, NEX, CPLX, NTT>;
-  const int64_t kp = kpad(K);
+  CHASE_REQUIRE(nops >= 1 && nops <= G, 1, "split product: bad number of products in one launch");
   const int ap = CPLX ? 2 : 1, bp = CPLX ? 3 : 1;
-  CUtensorMap ma = make_map(lpl, K, kp, M, l_slices_total * ap, BM);
-  CUtensorMap mb = make_map(rpl, K, kp, N, S * bp, Cf::BROWS);
+  // the parameter block is large for G > 1: build it in thread-local host memory
+  static thread_local GroupParams<G> gp;
+  int64_t tiles = 0;
+  for (int q = 0; q < nops; ++q) {
+    const ProductOp& o = ops[q];
+    const int64_t kp = kpad(o.K);
+    gp.tmA[q] = make_map(o.lpl, o.K, kp, o.M, o.l_slices_total * ap, BM);
+    gp.tmB[q] = make_map(o.rpl, o.K, kp, o.N, S * bp, Cf::BROWS);
+    const Epi& e = o.e;
+    gp.ep[q] = EpiArgs{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
+    gp.a_scale[q] = o.lsc;
+    gp.b_scale[q] = o.rsc;
+    gp.M[q] = (int)o.M;
+    gp.N[q] = (int)o.N;
+    gp.K[q] = (int)o.K;
+    gp.group_m[q] = std::max(1, o.group_m);
+    gp.tile_begin[q] = (int)tiles;
+    tiles += (int64_t)ceil_div(o.N, Cf::NCOLS) * (int64_t)ceil_div(o.M, BM);
+    CHASE_REQUIRE(tiles <= 0x7fffffff, 1, "split product: too many tiles");
+  }
+  gp.tile_begin[nops] = (int)tiles;
+  gp.nprob = nops;
+  if (tiles == 0) return;
   // once per instantiation, thread-safe (batched solves launch from several host threads)
   static std::once_flag attr_once;
-  cudaError_t attr_err = cudaSuccess;
+  static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [&]() {
-    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX, NTT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    attr_err = cudaFuncSetAttribute(oz_gemm_kernel<S, NEX, CPLX, NTT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     Cf::SMEM_BYTES);
   });
   CHASE_CUDA(attr_err);
-  EpiArgs ea{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
-  const int64_t tiles = (int64_t)ceil_div(N, Cf::NCOLS) * (int64_t)ceil_div(M, BM);
-  CHASE_REQUIRE(tiles <= 0x7fffffff, 1, "split product: too many tiles");
-  const int group_m = std::max(1, w.group_m);
   const bool timed = w.timing && w.ev_used + 2 <= (int)w.ev.size();
   if (timed) CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used], st));
-  oz_gemm_kernel<S, NEX, CPLX, NTT><<<(unsigned)tiles, NTHREADS, Cf::SMEM_BYTES, st>>>(
-      ma, mb, (int)M, (int)N, (int)K, lsc, rsc, ea, w.flags, group_m);
+  oz_gemm_kernel<S, NEX, CPLX, NTT, G><<<(unsigned)tiles, NTHREADS, Cf::SMEM_BYTES, st>>>(gp, w.flags);
   CHASE_CHECK_LAUNCH();
   if (timed) {
     CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used + 1], st));
     w.ev_used += 2;
   }
+}
+
+template <int S, int NEX, bool CPLX, int NTT>
+static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double* lsc, int l_slices_total,
+                   const void* rpl, const double* rsc, int64_t M, int64_t N, int64_t K, const Epi& e) {
+  ProductOp op{lpl, lsc, l_slices_total, rpl, rsc, M, N, K, e, w.group_m};
+  launch_ops<S, NEX, CPLX, NTT, 1>(st, w, &op, 1);
 }
 
 template <bool CPLX>
@@ -909,6 +958,28 @@ static void dispatch(cudaStream_t st, Workspace& w, int S_, const void* lpl, con
   else if (S_ == 6) launch<6, 5, CPLX, 80>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
   else if (S_ == 3) launch<3, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
   else launch<2, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+}
+
+template <typename T>
+void split_right(cudaStream_t st, Workspace& w, int mode, const T* B, int64_t ldb, int k, int64_t n) {
+  CHASE_REQUIRE(w.ready, 9, "split products not initialised");
+  CHASE_REQUIRE(k <= w.ne_max && n <= w.n_max, 1, "split_right: size exceeds the workspace");
+  split<T>(st, slices_for(mode, w.slices), 1, false, false, B, ldb, k, n, w.b_planes, w.b_scale);
+}
+
+template <bool CPLX>
+void launch_group(cudaStream_t st, Workspace& w, int mode, const ProductOp* ops, int nops) {
+  constexpr int G = 64;
+  const int S_ = slices_for(mode, w.slices);
+  for (int q0 = 0; q0 < nops; q0 += G) {
+    const int cnt = std::min(G, nops - q0);
+    for (int q = q0; q < q0 + cnt; ++q)
+      CHASE_REQUIRE(ops[q].K <= 65472, 1, "split products support K <= 65472 (int64 exact-level sums)");
+    if (S_ == 7) launch_ops<7, 5, CPLX, 80, G>(st, w, ops + q0, cnt);
+    else if (S_ == 6) launch_ops<6, 5, CPLX, 80, G>(st, w, ops + q0, cnt);
+    else if (S_ == 3) launch_ops<3, 0, CPLX, 128, G>(st, w, ops + q0, cnt);
+    else launch_ops<2, 0, CPLX, 128, G>(st, w, ops + q0, cnt);
+  }
 }
 
 template <typename T>
@@ -955,6 +1026,10 @@ template void gemm<double2>(cudaStream_t, Workspace&, Op, const double2*, int64_
                             int64_t, int64_t, const Epi&, int);
 template void hemm<double2>(cudaStream_t, Workspace&, const double2*, int64_t, int64_t, const double2*, int64_t, int,
                             const Epi&, int);
+template void split_right<double>(cudaStream_t, Workspace&, int, const double*, int64_t, int, int64_t);
+template void split_right<double2>(cudaStream_t, Workspace&, int, const double2*, int64_t, int, int64_t);
+template void launch_group<false>(cudaStream_t, Workspace&, int, const ProductOp*, int);
+template void launch_group<true>(cudaStream_t, Workspace&, int, const ProductOp*, int);
 
 }  // namespace oz
 }  // namespace chase

@@ -61,14 +61,17 @@ def test_batched_warm_start_sequence(pkg):
         assert max(mv[1][q], mv[2][q]) < mv[0][q]
 
 
-@pytest.mark.parametrize("workers", [1, 3])
-def test_batched_workers_uneven_sizes(pkg, workers):
-    """Concurrent workers (one stream and workspace each) solve a batch of uneven sizes; every problem
-    meets the eigenvalue and residual tolerance against a dense eigendecomposition, and the returned
-    start blocks warm-start a second, perturbed step."""
+@pytest.mark.parametrize("workers,grouped", [(1, 0), (3, 0), (1, 1), (3, 1)])
+def test_batched_workers_uneven_sizes(pkg, workers, grouped):
+    """A batch of uneven sizes, in the worker-pool mode (concurrent workers, one stream and workspace
+    each) and in the grouped mode (lockstep problems, one grouped filter launch per degree step, the
+    other stages on `workers` host threads): every problem meets the eigenvalue and residual tolerance
+    against a dense eigendecomposition, and the returned start blocks warm-start a second, perturbed
+    step."""
     ns = [160, 613, 96, 401, 257, 520, 333]
     probs = [G.problem_c4(pid, n) for pid, n in enumerate(ns)]
-    ctx = pkg.Chase(max(ns), max(p.ne for p in probs), complex_=True, opts={"batch_workers": workers})
+    ctx = pkg.Chase(max(ns), max(p.ne for p in probs), complex_=True,
+                    opts={"batch_workers": workers, "batch_grouped": grouped})
     A_host = [p.dense() for p in probs]
     A_dev = [dev(a) for a in A_host]
     V = [dev(p.V0) for p in probs]
