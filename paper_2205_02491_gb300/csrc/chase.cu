@@ -1503,13 +1503,27 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
   }
   c->stats = chase_stats_t{};
   oz::invalidate(c->ozw);
-  std::vector<cudaEvent_t> evs;
-  auto event = [&]() {
+  // two cohorts of about equal filter work (n^3 per problem), whose stages alternate: while one cohort's
+  // grouped filter runs on the batch stream, the other cohort's QR / Rayleigh-Ritz / bookkeeping run on
+  // their own streams, so the latency-bound per-problem stages overlap the tensor-core launches
+  std::vector<int> order(nprob);
+  for (int p = 0; p < nprob; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  std::vector<int> cohort[2];
+  double work[2] = {0.0, 0.0};
+  for (int p : order) {
+    const int h = work[0] <= work[1] ? 0 : 1;
+    cohort[h].push_back(p);
+    work[h] += (double)n[p] * (double)n[p] * (double)n[p];
+  }
+  std::vector<cudaEvent_t> evs;  // destroyed at the end (a destroyed event that a stream still waits on is fine)
+  auto event = [&](unsigned flags) {
     cudaEvent_t e = nullptr;
-    CHASE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CHASE_CUDA(cudaEventCreateWithFlags(&e, flags));
     evs.push_back(e);
     return e;
   };
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> filter_times;
   struct FilterPlan {
     int p;
     double cc;
@@ -1517,118 +1531,131 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
     int f = 0;
     int64_t mv = 0;
   };
-  try {
-    for (int it = 0; it < c->opts.maxiter; ++it) {
-      std::vector<int> active;
-      for (int p = 0; p < nprob; ++p)
-        if (!failed[p] && !R[p].done(c->opts.maxiter)) active.push_back(p);
-      if (active.empty()) break;
-      // ---- line 4 for every active problem: one grouped launch per degree step (per arithmetic)
-      Timer tf(c, 1, &c->stats.ms_filter);
-      std::vector<FilterPlan> plans;
-      int smax = 0;
-      for (int p : active) {
-        chase_ctx* sc = c->slots[p];
-        ++R[p].it;
-        cudaEvent_t e = event();
-        CHASE_CUDA(cudaEventRecord(e, sc->stream));
-        CHASE_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
-        if (R[p].k() <= 0) continue;
-        FilterPlan fp;
-        fp.p = p;
-        double ee;
-        const int mmax = R[p].m[R[p].k() - 1];
-        filter_coeffs(R[p].b_sup, R[p].mu_1, R[p].mu_ne, mmax, fp.cc, ee, fp.al, fp.be);
-        // the digit planes of A: computed once per solve (cached in the problem's workspace)
-        oz::prepare_A<T>(c->stream, sc->ozw, R[p].A, R[p].n, R[p].lda, CHASE_FP64);
-        smax = std::max(smax, mmax);
-        plans.push_back(std::move(fp));
-      }
-      oz::timing_begin(c->ozw);
-      std::vector<oz::ProductOp> ops_hi, ops_lo;
-      for (int sstep = 1; sstep <= smax; ++sstep) {
-        ops_hi.clear();
-        ops_lo.clear();
-        for (FilterPlan& fp : plans) {
-          const int p = fp.p;
-          auto& r = R[p];
-          chase_ctx* sc = c->slots[p];
-          const int k = r.k();
-          while (fp.f < k && r.m[fp.f] < sstep) ++fp.f;
-          const int cols = k - fp.f;
-          if (cols <= 0) continue;
-          fp.mv += cols;
-          T* Vact = (T*)sc->V + (int64_t)r.l * r.n;
-          T* T1act = (T*)sc->T1 + (int64_t)r.l * r.n;
-          T* Bb[2] = {Vact, T1act};
-          T* out = Bb[sstep & 1] + (int64_t)fp.f * r.n;
-          const T* in = Bb[(sstep - 1) & 1] + (int64_t)fp.f * r.n;
-          const int fmode = r.fmode();
-          oz::split_right<T>(c->stream, sc->ozw, fmode, in, r.n, cols, r.n);
-          Epi e;
-          e.C = out;
-          e.ldc = r.n;
-          e.alpha = fp.al[sstep];
-          e.Y = in;
-          e.ldy = r.n;
-          e.gamma = -fp.al[sstep] * fp.cc;
-          if (sstep >= 2) {
-            e.Z = out;
-            e.ldz = r.n;
-            e.beta = fp.be[sstep];
-          }
-          oz::ProductOp op{sc->ozw.a_planes, sc->ozw.a_scale, sc->ozw.slices, sc->ozw.b_planes, sc->ozw.b_scale,
-                           r.n, cols, r.n, e, c->ozw.group_m};
-          (fmode == CHASE_FP64 ? ops_hi : ops_lo).push_back(op);
-          sc->stats.filter_launches++;
-        }
-        if (!ops_hi.empty()) oz::launch_group<CPLX>(c->stream, c->ozw, CHASE_FP64, ops_hi.data(), (int)ops_hi.size());
-        if (!ops_lo.empty()) {
-          // the low-precision problems of one batch share its mode
-          oz::launch_group<CPLX>(c->stream, c->ozw, mode, ops_lo.data(), (int)ops_lo.size());
-        }
-      }
+  auto active_of = [&](int h) {
+    std::vector<int> a;
+    for (int p : cohort[h])
+      if (!failed[p] && !R[p].done(c->opts.maxiter)) a.push_back(p);
+    return a;
+  };
+  // line 4 for every active problem of a cohort, enqueued on the batch stream: one grouped launch per
+  // degree step (and arithmetic); returns without waiting for the device
+  auto enqueue_filter = [&](const std::vector<int>& active) {
+    cudaEvent_t t0 = event(cudaEventDefault), t1 = event(cudaEventDefault);
+    std::vector<FilterPlan> plans;
+    int smax = 0;
+    for (int p : active) {
+      chase_ctx* sc = c->slots[p];
+      ++R[p].it;
+      cudaEvent_t e = event(cudaEventDisableTiming);
+      CHASE_CUDA(cudaEventRecord(e, sc->stream));
+      CHASE_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
+      if (R[p].k() <= 0) continue;
+      FilterPlan fp;
+      fp.p = p;
+      double ee;
+      const int mmax = R[p].m[R[p].k() - 1];
+      filter_coeffs(R[p].b_sup, R[p].mu_1, R[p].mu_ne, mmax, fp.cc, ee, fp.al, fp.be);
+      smax = std::max(smax, mmax);
+      plans.push_back(std::move(fp));
+    }
+    CHASE_CUDA(cudaEventRecord(t0, c->stream));
+    // the digit planes of A: computed once per solve (cached in the problem's workspace)
+    for (FilterPlan& fp : plans) oz::prepare_A<T>(c->stream, c->slots[fp.p]->ozw, R[fp.p].A, R[fp.p].n, R[fp.p].lda,
+                                                  CHASE_FP64);
+    std::vector<oz::ProductOp> ops_hi, ops_lo;
+    for (int sstep = 1; sstep <= smax; ++sstep) {
+      ops_hi.clear();
+      ops_lo.clear();
       for (FilterPlan& fp : plans) {
         auto& r = R[fp.p];
         chase_ctx* sc = c->slots[fp.p];
         const int k = r.k();
+        while (fp.f < k && r.m[fp.f] < sstep) ++fp.f;
+        const int cols = k - fp.f;
+        if (cols <= 0) continue;
+        fp.mv += cols;
         T* Vact = (T*)sc->V + (int64_t)r.l * r.n;
         T* T1act = (T*)sc->T1 + (int64_t)r.l * r.n;
-        dim3 grid(std::min<unsigned>(ceil_div(r.n, 256), 64), k);
-        gather_odd_kernel<T><<<grid, 256, 0, c->stream>>>(r.n, sc->deg, Vact, r.n, T1act, r.n);
-        CHASE_CHECK_LAUNCH();
-        Solver<T>(sc).count_matvecs(r, fp.mv);
-      }
-      cudaEvent_t done_f = event();
-      CHASE_CUDA(cudaEventRecord(done_f, c->stream));
-      for (int p : active) CHASE_CUDA(cudaStreamWaitEvent(c->slots[p]->stream, done_f, 0));
-      {
-        int nl = 0;
-        const double ms = oz::timing_collect(c->ozw, &nl);
-        c->stats.ms_filter_kernel += ms;
-        c->stats.filter_kernel_launches += nl;
-      }
-      tf.stop();
-      CHASE_REQUIRE(oz::read_flags(c->stream, c->ozw) == 0, CHASE_ERR_TIMEOUT,
-                    "a grouped tensor-core product hit its wait limit");
-      // ---- lines 5-14 per problem
-      std::mutex mu;
-      parallel_for(c->device, threads, (int)active.size(), [&](int i) {
-        const int p = active[i];
-        try {
-          Solver<T>(c->slots[p]).after_filter(R[p]);
-        } catch (const chase::Error& e) {
-          std::lock_guard<std::mutex> lock(mu);
-          fail_problem(p, e);
+        T* Bb[2] = {Vact, T1act};
+        T* out = Bb[sstep & 1] + (int64_t)fp.f * r.n;
+        const T* in = Bb[(sstep - 1) & 1] + (int64_t)fp.f * r.n;
+        const int fmode = r.fmode();
+        oz::split_right<T>(c->stream, sc->ozw, fmode, in, r.n, cols, r.n);
+        Epi e;
+        e.C = out;
+        e.ldc = r.n;
+        e.alpha = fp.al[sstep];
+        e.Y = in;
+        e.ldy = r.n;
+        e.gamma = -fp.al[sstep] * fp.cc;
+        if (sstep >= 2) {
+          e.Z = out;
+          e.ldz = r.n;
+          e.beta = fp.be[sstep];
         }
-      });
-      for (cudaEvent_t e : evs) cudaEventDestroy(e);
-      evs.clear();
+        oz::ProductOp op{sc->ozw.a_planes, sc->ozw.a_scale, sc->ozw.slices, sc->ozw.b_planes, sc->ozw.b_scale,
+                         r.n, cols, r.n, e, c->ozw.group_m};
+        (fmode == CHASE_FP64 ? ops_hi : ops_lo).push_back(op);
+        sc->stats.filter_launches++;
+      }
+      if (!ops_hi.empty()) oz::launch_group<CPLX>(c->stream, c->ozw, CHASE_FP64, ops_hi.data(), (int)ops_hi.size());
+      // the low-precision problems of one batch share its mode
+      if (!ops_lo.empty()) oz::launch_group<CPLX>(c->stream, c->ozw, mode, ops_lo.data(), (int)ops_lo.size());
     }
+    for (FilterPlan& fp : plans) {
+      auto& r = R[fp.p];
+      chase_ctx* sc = c->slots[fp.p];
+      const int k = r.k();
+      T* Vact = (T*)sc->V + (int64_t)r.l * r.n;
+      T* T1act = (T*)sc->T1 + (int64_t)r.l * r.n;
+      dim3 grid(std::min<unsigned>(ceil_div(r.n, 256), 64), k);
+      gather_odd_kernel<T><<<grid, 256, 0, c->stream>>>(r.n, sc->deg, Vact, r.n, T1act, r.n);
+      CHASE_CHECK_LAUNCH();
+      Solver<T>(sc).count_matvecs(r, fp.mv);
+    }
+    CHASE_CUDA(cudaEventRecord(t1, c->stream));
+    filter_times.emplace_back(t0, t1);
+    cudaEvent_t done_f = event(cudaEventDisableTiming);
+    CHASE_CUDA(cudaEventRecord(done_f, c->stream));
+    for (int p : active) CHASE_CUDA(cudaStreamWaitEvent(c->slots[p]->stream, done_f, 0));
+  };
+  // lines 5-14 per problem of a cohort, on the host threads (each problem on its own stream)
+  auto after = [&](const std::vector<int>& active) {
+    std::mutex mu;
+    parallel_for(c->device, threads, (int)active.size(), [&](int i) {
+      const int p = active[i];
+      try {
+        Solver<T>(c->slots[p]).after_filter(R[p]);
+      } catch (const chase::Error& e) {
+        std::lock_guard<std::mutex> lock(mu);
+        fail_problem(p, e);
+      }
+    });
+  };
+  try {
+    std::vector<int> act[2] = {active_of(0), active_of(1)};
+    for (int h = 0; h < 2; ++h)
+      if (!act[h].empty()) enqueue_filter(act[h]);
+    for (int h = 0; !act[0].empty() || !act[1].empty(); h ^= 1) {
+      if (act[h].empty()) continue;
+      after(act[h]);
+      act[h] = active_of(h);
+      if (!act[h].empty()) enqueue_filter(act[h]);
+    }
+    CHASE_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto& t : filter_times) {
+      float ms = 0.f;
+      CHASE_CUDA(cudaEventElapsedTime(&ms, t.first, t.second));
+      c->stats.ms_filter += ms;
+    }
+    CHASE_REQUIRE(oz::read_flags(c->stream, c->ozw) == 0, CHASE_ERR_TIMEOUT,
+                  "a grouped tensor-core product hit its wait limit");
   } catch (...) {
+    cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
     throw;
   }
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
   // results: eigenvalues, eigenvectors followed by the rest of the search block (next start block)
   {
     std::mutex mu;

@@ -4,12 +4,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <vector>
 
 #include "kernels.h"
 
 namespace chase {
 namespace oz {
+
+// Launch configuration of the split-product kernel chosen by measurement (see tune_pick in oz_gemm.cu):
+// the tile width NT of the mixed modes (128 or 256 columns) and the tile-order group size.
+struct LaunchCfg {
+  int nt = 0;       // 0: the mode's fixed width
+  int group_m = 8;
+};
+
+// One size class of the tuner: candidates are timed on consecutive launches of that class (the degree
+// steps of a filter repeat one shape), then the fastest is kept for the context's lifetime.
+struct TuneEntry {
+  int next = 0;          // candidates launched so far
+  int best = -1;         // index of the chosen candidate once every one has been timed
+  std::vector<cudaEvent_t> ev;  // start/stop pair per candidate
+};
 
 struct Workspace {
   bool ready = false;
@@ -24,7 +40,9 @@ struct Workspace {
   double* l_scale = nullptr;  // per-row scale of the general left operand
   double* b_scale = nullptr;  // per-column scale of the right operand
   int* flags = nullptr;       // device error flags of the bounded waits
-  int group_m = 8;            // row blocks per tile group of the split-product launch order
+  int group_m = 8;            // row blocks per tile group of the split-product launch order (untuned launches)
+  bool autotune = true;       // choose LaunchCfg per size class by timing the candidates
+  std::map<uint64_t, TuneEntry> tune;  // size class -> measurements and choice
   // optional CUDA-event timing of the product kernels (filter roofline)
   bool timing = false;
   std::vector<cudaEvent_t> ev;
@@ -51,6 +69,8 @@ bool available();
 int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices);
 void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices);
 void destroy(Workspace& w);
+// the tuner's choices so far: (size-class key, candidate index) pairs, for reports
+std::vector<std::pair<uint64_t, int>> tuned(const Workspace& w);
 void invalidate(Workspace& w);
 // start recording event pairs around every product kernel; collect returns (ms, launches)
 void timing_begin(Workspace& w);

@@ -800,6 +800,9 @@ void destroy(Workspace& w) {
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& e : w.ev) cudaEventDestroy(e);
+  for (auto& kv : w.tune)
+    for (auto& e : kv.second.ev)
+      if (e) cudaEventDestroy(e);
   w = Workspace{};
 }
 
@@ -890,11 +893,77 @@ void invalidate(Workspace& w) {
 
 // C(M x N) = L(M x K) R(K x N) from digit planes (left: rows = M vectors of length K, right:
 // rows = N vectors of length K), split with l_slices_total / S slices respectively.
+// ---------------------------------------------------------------- launch-configuration tuner
+// Candidates per arithmetic: the FP64 kernels (NT fixed at 80 by TMEM) try the tile-order group sizes;
+// the mixed kernels (one accumulator) also try the 256-column tile, which halves the instructions per
+// unit of tensor work.
+static const LaunchCfg kCandFP64[] = {{0, 2}, {0, 4}, {0, 8}, {0, 16}, {0, 32}};
+static const LaunchCfg kCandMixed[] = {{128, 4}, {128, 16}, {256, 4}, {256, 16}};
+
+static int log2_bucket(int64_t x) {
+  int b = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+// Size class of a launch: arithmetic, element type, grouped or not, and the log2 buckets of the shape.
+static uint64_t tune_key(int S_, bool cplx, bool grouped, int64_t M, int64_t N, int64_t K) {
+  return ((uint64_t)S_ << 56) | ((uint64_t)cplx << 55) | ((uint64_t)grouped << 54) |
+         ((uint64_t)log2_bucket(M) << 36) | ((uint64_t)log2_bucket(N) << 18) | (uint64_t)log2_bucket(K);
+}
+
+// The configuration for the next launch of a size class.  Until every candidate has been timed, each
+// launch takes the next candidate and gets an event pair (*ev_out); the first launch after that reads
+// the times (one event synchronisation per size class and context) and keeps the fastest.
+static LaunchCfg tune_pick(Workspace& w, uint64_t key, bool mixed, cudaEvent_t** ev_out) {
+  const LaunchCfg* cand = mixed ? kCandMixed : kCandFP64;
+  const int nc = mixed ? (int)(sizeof(kCandMixed) / sizeof(kCandMixed[0]))
+                       : (int)(sizeof(kCandFP64) / sizeof(kCandFP64[0]));
+  *ev_out = nullptr;
+  if (!w.autotune) {
+    LaunchCfg d = mixed ? LaunchCfg{128, w.group_m} : LaunchCfg{0, w.group_m};
+    return d;
+  }
+  TuneEntry& t = w.tune[key];
+  if (t.best >= 0) return cand[t.best];
+  if (t.ev.empty()) {
+    t.ev.resize(2 * nc, nullptr);
+    for (auto& e : t.ev) CHASE_CUDA(cudaEventCreate(&e));
+  }
+  if (t.next < nc) {
+    *ev_out = &t.ev[2 * t.next];
+    return cand[t.next++];
+  }
+  float best_ms = 0.f;
+  int best = 0;
+  for (int i = 0; i < nc; ++i) {
+    CHASE_CUDA(cudaEventSynchronize(t.ev[2 * i + 1]));
+    float ms = 0.f;
+    CHASE_CUDA(cudaEventElapsedTime(&ms, t.ev[2 * i], t.ev[2 * i + 1]));
+    if (i == 0 || ms < best_ms) {
+      best_ms = ms;
+      best = i;
+    }
+  }
+  t.best = best;
+  return cand[best];
+}
+
+std::vector<std::pair<uint64_t, int>> tuned(const Workspace& w) {
+  std::vector<std::pair<uint64_t, int>> out;
+  for (const auto& kv : w.tune)
+    if (kv.second.best >= 0) out.emplace_back(kv.first, kv.second.best);
+  return out;
+}
+
 // Products of one launch: up to G of them, each C = L R from its digit planes (left: rows = M vectors of
 // length K, split into l_slices_total slices of which the first S are used; right: rows = N vectors of
 // length K, S slices).
 template <int S, int NEX, bool CPLX, int NTT, int G>
-static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int nops) {
+static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int nops, cudaEvent_t* tune_ev = nullptr) {
   using Cf = Cfg<S, NEX, CPLX, NTT>;
   CHASE_REQUIRE(nops >= 1 && nops <= G, 1, "split product: bad number of products in one launch");
   const int ap = CPLX ? 2 : 1, bp = CPLX ? 3 : 1;
@@ -931,8 +1000,10 @@ static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int 
   CHASE_CUDA(attr_err);
   const bool timed = w.timing && w.ev_used + 2 <= (int)w.ev.size();
   if (timed) CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used], st));
+  if (tune_ev) CHASE_CUDA(cudaEventRecord(tune_ev[0], st));
   oz_gemm_kernel<S, NEX, CPLX, NTT, G><<<(unsigned)tiles, NTHREADS, Cf::SMEM_BYTES, st>>>(gp, w.flags);
   CHASE_CHECK_LAUNCH();
+  if (tune_ev) CHASE_CUDA(cudaEventRecord(tune_ev[1], st));
   if (timed) {
     CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used + 1], st));
     w.ev_used += 2;
@@ -941,9 +1012,10 @@ static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int 
 
 template <int S, int NEX, bool CPLX, int NTT>
 static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double* lsc, int l_slices_total,
-                   const void* rpl, const double* rsc, int64_t M, int64_t N, int64_t K, const Epi& e) {
-  ProductOp op{lpl, lsc, l_slices_total, rpl, rsc, M, N, K, e, w.group_m};
-  launch_ops<S, NEX, CPLX, NTT, 1>(st, w, &op, 1);
+                   const void* rpl, const double* rsc, int64_t M, int64_t N, int64_t K, const Epi& e,
+                   int group_m, cudaEvent_t* tune_ev) {
+  ProductOp op{lpl, lsc, l_slices_total, rpl, rsc, M, N, K, e, group_m};
+  launch_ops<S, NEX, CPLX, NTT, 1>(st, w, &op, 1, tune_ev);
 }
 
 template <bool CPLX>
@@ -953,11 +1025,22 @@ static void dispatch(cudaStream_t st, Workspace& w, int S_, const void* lpl, con
   // a narrow right operand (up to 8 complex or 16 real columns: the Lanczos block) takes the N = 16 tile, so
   // the launch streams the left planes once without computing unused accumulator columns
   const bool narrow = N <= (CPLX ? 8 : 16);
-  if (S_ == 7 && narrow) launch<7, 5, CPLX, 16>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
-  else if (S_ == 7) launch<7, 5, CPLX, 80>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
-  else if (S_ == 6) launch<6, 5, CPLX, 80>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
-  else if (S_ == 3) launch<3, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
-  else launch<2, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, w.b_planes, w.b_scale, M, N, K, e);
+  const void* rp = w.b_planes;
+  const double* rs = w.b_scale;
+  if (narrow && S_ >= 6) {
+    // one column tile: the tile order is irrelevant
+    if (S_ == 7) launch<7, 5, CPLX, 16>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, 1, nullptr);
+    else launch<6, 5, CPLX, 16>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, 1, nullptr);
+    return;
+  }
+  cudaEvent_t* ev = nullptr;
+  const LaunchCfg cfg = tune_pick(w, tune_key(S_, CPLX, false, M, N, K), S_ <= 3, &ev);
+  if (S_ == 7) launch<7, 5, CPLX, 80>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, cfg.group_m, ev);
+  else if (S_ == 6) launch<6, 5, CPLX, 80>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, cfg.group_m, ev);
+  else if (S_ == 3 && cfg.nt == 256) launch<3, 0, CPLX, 256>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, cfg.group_m, ev);
+  else if (S_ == 3) launch<3, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, cfg.group_m, ev);
+  else if (cfg.nt == 256) launch<2, 0, CPLX, 256>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, cfg.group_m, ev);
+  else launch<2, 0, CPLX, 128>(st, w, lpl, lsc, l_slices_total, rp, rs, M, N, K, e, cfg.group_m, ev);
 }
 
 template <typename T>
@@ -971,14 +1054,28 @@ template <bool CPLX>
 void launch_group(cudaStream_t st, Workspace& w, int mode, const ProductOp* ops, int nops) {
   constexpr int G = 64;
   const int S_ = slices_for(mode, w.slices);
+  std::vector<ProductOp> chunk;
   for (int q0 = 0; q0 < nops; q0 += G) {
     const int cnt = std::min(G, nops - q0);
-    for (int q = q0; q < q0 + cnt; ++q)
+    // size class of a grouped launch: its total work in row blocks x columns x K
+    int64_t rows = 0, cols = 0, kk = 0;
+    for (int q = q0; q < q0 + cnt; ++q) {
       CHASE_REQUIRE(ops[q].K <= 65472, 1, "split products support K <= 65472 (int64 exact-level sums)");
-    if (S_ == 7) launch_ops<7, 5, CPLX, 80, G>(st, w, ops + q0, cnt);
-    else if (S_ == 6) launch_ops<6, 5, CPLX, 80, G>(st, w, ops + q0, cnt);
-    else if (S_ == 3) launch_ops<3, 0, CPLX, 128, G>(st, w, ops + q0, cnt);
-    else launch_ops<2, 0, CPLX, 128, G>(st, w, ops + q0, cnt);
+      rows += ops[q].M;
+      cols = std::max(cols, ops[q].N);
+      kk = std::max(kk, ops[q].K);
+    }
+    cudaEvent_t* ev = nullptr;
+    const LaunchCfg cfg = tune_pick(w, tune_key(S_, CPLX, true, rows, cols, kk), S_ <= 3, &ev);
+    chunk.assign(ops + q0, ops + q0 + cnt);
+    for (auto& o : chunk) o.group_m = cfg.group_m;
+    const ProductOp* cp = chunk.data();
+    if (S_ == 7) launch_ops<7, 5, CPLX, 80, G>(st, w, cp, cnt, ev);
+    else if (S_ == 6) launch_ops<6, 5, CPLX, 80, G>(st, w, cp, cnt, ev);
+    else if (S_ == 3 && cfg.nt == 256) launch_ops<3, 0, CPLX, 256, G>(st, w, cp, cnt, ev);
+    else if (S_ == 3) launch_ops<3, 0, CPLX, 128, G>(st, w, cp, cnt, ev);
+    else if (cfg.nt == 256) launch_ops<2, 0, CPLX, 256, G>(st, w, cp, cnt, ev);
+    else launch_ops<2, 0, CPLX, 128, G>(st, w, cp, cnt, ev);
   }
 }
 
