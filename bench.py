@@ -344,7 +344,12 @@ def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4, ws=1, rank=0
         flops += fl
         rec = {"seconds": round(dt, 3), "matvecs": int(sum(st["matvecs"] for st in stats)),
                "iterations_max": int(max(st["iterations"] for st in stats)),
-               "max_resid": max(st["max_resid"] for st in stats), "filter_tflops_wall": fl / dt / 1e12}
+               "max_resid": max(st["max_resid"] for st in stats), "filter_tflops_wall": fl / dt / 1e12,
+               # GPU time of the grouped filter launches (batch context) and the per-problem stage times
+               # summed over problems (each on its own stream, overlapping one another)
+               "filter_gpu_ms": round(ctx.stats()["ms_filter"], 1),
+               "stage_ms_sum": {k: round(sum(st[k] for st in stats), 1) for k in ("ms_lanczos", "ms_qr", "ms_rr",
+                                                                                 "ms_resid")}}
         if step == 0:  # exact spectrum known before the first perturbation
             rec["max_abs_eig_err_vs_exact"] = float(max(np.max(np.abs(w.cpu().numpy() - p.lam[:p.nev])) for w, p in
                                                         zip(wvals, probs)))

@@ -94,8 +94,8 @@ typedef struct {
   int minres_iterations;        /* MINRES iterations of the last chase_backward */
   int rr_clusters;              /* eigenvalue clusters solved exactly in the Rayleigh-Ritz eigensolves */
   int rr_fallbacks;             /* Rayleigh-Ritz eigensolves that fell back to the FP64 Jacobi */
-  int qr_replaced;              /* numerically dependent columns of filtered blocks that the QR step
-                                   replaced by seeded random vectors */
+  int qr_householder;           /* QR steps whose block was numerically rank deficient for Cholesky-QR and
+                                   went to the Householder QR */
   int filter_reorth;            /* orthonormalisations inside equal-degree filters whose amplification
                                    would exceed 1e7 (the filtered span is unchanged) */
 } chase_stats_t;
@@ -200,9 +200,10 @@ chase_status chase_filter(chase_ctx* ctx, const void* A_dev, int64_t n, int64_t 
 
 /* Algorithm 1, line 5: orthonormalise X (n x ncols, ld ldx) in place by
  * Cholesky-QR2 (shifted Cholesky-QR3 fallback); the first nlocked columns are
- * assumed orthonormal and are left unchanged.  A column whose remainder after
- * the columns before it is at rounding level (numerically dependent) is first
- * replaced by a seeded random vector (counted in chase_stats_t.qr_replaced). */
+ * assumed orthonormal and are left unchanged.  A block that is numerically
+ * rank deficient for Cholesky-QR (a column's remainder after the columns before
+ * it within the rounding of the Gram matrix) is first orthonormalised by a
+ * blocked Householder QR (counted in chase_stats_t.qr_householder). */
 chase_status chase_qr(chase_ctx* ctx, void* X_dev, int64_t n, int64_t ldx, int ncols, int nlocked);
 
 /* Algorithm 1, lines 6-7: Rayleigh-Ritz on the ncols orthonormal columns Q

@@ -508,6 +508,118 @@ void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* la
   CHASE_CHECK_LAUNCH();
 }
 
+// ============================================================== Householder QR building blocks
+// Reflector of one column segment x (length m): alpha = -ph ||x|| with ph = x0/|x0| (1 for x0 = 0),
+// v = x - alpha e1 written over x, H = I - tau v v^H with tau = 2/||v||^2 (0 for x = 0), so H x = alpha e1.
+template <typename T>
+__global__ void __launch_bounds__(1024) householder_vec_kernel(int64_t m, T* x, T* alpha, double* tau) {
+  using s = S<T>;
+  __shared__ double red[32];
+  double ss = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) ss += s::abs2(x[i]);
+  ss = warp_sum(ss);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    const T x0 = x[0];
+    const double a0 = sqrt(s::abs2(x0));
+    const double nrm = sqrt(t);
+    const T ph = a0 > 0.0 ? s::scale(x0, 1.0 / a0) : s::one();
+    alpha[0] = s::scale(ph, -nrm);
+    const T v0 = s::scale(ph, a0 + nrm);
+    const double vv = t - a0 * a0 + (a0 + nrm) * (a0 + nrm);
+    tau[0] = vv > 0.0 ? 2.0 / vv : 0.0;
+    x[0] = v0;
+  }
+}
+
+// X (m x ncols, ld ldx) <- (I - tau v v^H) X, one block per column.
+template <typename T>
+__global__ void householder_apply_kernel(int64_t m, const T* __restrict__ v, T* X, int64_t ldx, const double* tau) {
+  using s = S<T>;
+  __shared__ double red_re[32], red_im[32];
+  __shared__ T w_sh;
+  T* x = X + (int64_t)blockIdx.x * ldx;
+  T acc = s::zero();
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) acc = s::fmac(v[i], x[i], acc);  // conj(v) x
+  double re = warp_sum(s::re(acc)), im = warp_sum(s::im(acc));
+  if ((threadIdx.x & 31) == 0) {
+    red_re[threadIdx.x >> 5] = re;
+    red_im[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0, ti = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tr += red_re[w];
+      ti += red_im[w];
+    }
+    w_sh = s::scale(s::make(tr, ti), tau[0]);
+  }
+  __syncthreads();
+  const T w = w_sh;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) x[i] = s::sub(x[i], s::mul(v[i], w));
+}
+
+// Panel reflectors with explicit zeros: V[i, j] = Xp[i, j] for i >= j, 0 above (m x pb, ld ldv).
+template <typename T>
+__global__ void reflector_panel_kernel(int64_t m, const T* __restrict__ Xp, int64_t ldx, T* V, int64_t ldv) {
+  const int j = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    V[i + (int64_t)j * ldv] = i < j ? S<T>::zero() : Xp[i + (int64_t)j * ldx];
+}
+
+// Compact-WY factor of H_1 ... H_pb = I - V Tm V^H (forward, column-wise): Tm upper triangular, Tm_jj = tau_j,
+// Tm(0:j, j) = -tau_j Tm(0:j, 0:j) Gv(0:j, j) with Gv = V^H V (pb x pb, ld pb).  One thread.
+template <typename T>
+__global__ void householder_T_kernel(int pb, const T* __restrict__ Gv, const double* __restrict__ tau, T* Tm,
+                                     int64_t ldt) {
+  using s = S<T>;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int j = 0; j < pb; ++j) {
+    for (int i = 0; i < j; ++i) {
+      T acc = s::zero();
+      for (int l = i; l < j; ++l) acc = s::add(acc, s::mul(Tm[i + (int64_t)l * ldt], Gv[l + (int64_t)j * pb]));
+      Tm[i + (int64_t)j * ldt] = s::scale(acc, -tau[j]);
+    }
+    Tm[j + (int64_t)j * ldt] = s::make(tau[j], 0.0);
+    for (int i = j + 1; i < pb; ++i) Tm[i + (int64_t)j * ldt] = s::zero();
+  }
+}
+
+template <typename T> __global__ void identity_rect_kernel(int64_t n, int k, T* Q, int64_t ldq) {
+  const int j = blockIdx.y;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    Q[i + (int64_t)j * ldq] = (i == j) ? S<T>::one() : S<T>::zero();
+}
+
+template <typename T> void householder_vec(cudaStream_t st, int64_t m, T* x, T* alpha, double* tau) {
+  householder_vec_kernel<T><<<1, 1024, 0, st>>>(m, x, alpha, tau);
+  CHASE_CHECK_LAUNCH();
+}
+template <typename T>
+void householder_apply(cudaStream_t st, int64_t m, const T* v, T* X, int64_t ldx, int ncols, const double* tau) {
+  if (ncols <= 0) return;
+  householder_apply_kernel<T><<<ncols, 256, 0, st>>>(m, v, X, ldx, tau);
+  CHASE_CHECK_LAUNCH();
+}
+template <typename T> void reflector_panel(cudaStream_t st, int64_t m, int pb, const T* Xp, int64_t ldx, T* V, int64_t ldv) {
+  dim3 grid(std::min<unsigned>(ceil_div(m, 256), 64), pb);
+  reflector_panel_kernel<T><<<grid, 256, 0, st>>>(m, Xp, ldx, V, ldv);
+  CHASE_CHECK_LAUNCH();
+}
+template <typename T> void householder_T(cudaStream_t st, int pb, const T* Gv, const double* tau, T* Tm, int64_t ldt) {
+  householder_T_kernel<T><<<1, 32, 0, st>>>(pb, Gv, tau, Tm, ldt);
+  CHASE_CHECK_LAUNCH();
+}
+template <typename T> void identity_rect(cudaStream_t st, int64_t n, int k, T* Q, int64_t ldq) {
+  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 64), k);
+  identity_rect_kernel<T><<<grid, 256, 0, st>>>(n, k, Q, ldq);
+  CHASE_CHECK_LAUNCH();
+}
+
 // ============================================================== seeded Hermitian perturbation
 // Counter-based Gaussian: SplitMix64 (Steele, Lea & Flood 2014) as a hash of (seed, counter), two 53-bit
 // uniforms per draw, Box-Muller.  G_ij (complex) uses counter 2 (i + j n) and 2 (i + j n) + 1; real uses one
@@ -555,28 +667,6 @@ __global__ void perturb_kernel(T* A, int64_t n, int64_t lda, double eps, unsigne
   }
 }
 
-// Columns flagged in depflags (depflags[j] != 0) of X (n x k) get fresh standard (complex) Gaussian
-// entries from the counter-based generator above, counter i + j n.
-template <typename T>
-__global__ void fill_dependent_cols_kernel(int64_t n, T* X, int64_t ldx, const int* depflags, unsigned long long seed) {
-  using s = S<T>;
-  const int j = blockIdx.y;
-  if (!depflags[j]) return;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double2 g = normal_pair(seed, (unsigned long long)(i + (int64_t)j * n));
-    X[i + (int64_t)j * ldx] = s::cplx ? s::make(0.7071067811865476 * g.x, 0.7071067811865476 * g.y) : s::make(g.x, 0.0);
-  }
-}
-
-template <typename T>
-void fill_dependent_cols(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const int* depflags,
-                         unsigned long long seed) {
-  if (k <= 0) return;
-  dim3 grid(std::min<unsigned>(ceil_div(n, 256), 64), (unsigned)k);
-  fill_dependent_cols_kernel<T><<<grid, 256, 0, st>>>(n, X, ldx, depflags, seed);
-  CHASE_CHECK_LAUNCH();
-}
-
 template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda, double eps, unsigned long long seed) {
   CHASE_REQUIRE(n <= 65535, 1, "perturbation supports n <= 65535");
   dim3 grid(ceil_div(n, 256), (unsigned)n);
@@ -597,7 +687,11 @@ template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda
   template void add_diag<T>(cudaStream_t, int, T*, int64_t, const double*, double);                               \
   template void hermitianize<T>(cudaStream_t, int, T*, int64_t);                                                  \
   template void potrf_lower<T>(cudaStream_t, int, T*, int64_t, int*, T*, int64_t, double, int*);                   \
-  template void fill_dependent_cols<T>(cudaStream_t, int64_t, int, T*, int64_t, const int*, unsigned long long);  \
+  template void householder_vec<T>(cudaStream_t, int64_t, T*, T*, double*);                                      \
+  template void householder_apply<T>(cudaStream_t, int64_t, const T*, T*, int64_t, int, const double*);            \
+  template void reflector_panel<T>(cudaStream_t, int64_t, int, const T*, int64_t, T*, int64_t);                   \
+  template void householder_T<T>(cudaStream_t, int, const T*, const double*, T*, int64_t);                         \
+  template void identity_rect<T>(cudaStream_t, int64_t, int, T*, int64_t);                                         \
   template void trsm_right_lh<T>(cudaStream_t, int64_t, int, T*, int64_t, const T*, int64_t, T*, int64_t);        \
   template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int); \
   template void zero_upper<T>(cudaStream_t, int, T*, int64_t);                                                    \

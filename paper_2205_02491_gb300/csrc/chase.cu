@@ -72,7 +72,7 @@ struct chase_ctx {
   int* info = nullptr;
   int* status_dev = nullptr;
   int* qr_dep = nullptr;             // Cholesky-QR dependent-column flags (count, then ne_max flags)
-  unsigned long long qr_fill_calls = 0;  // seeds the random refill of dependent columns
+  void* hh = nullptr;                // Householder QR scratch: 3 x 32 x ne_max + ne_max + 1024 scalars
   oz::Workspace ozw{};
   // result state
   bool have_result = false;
@@ -348,6 +348,89 @@ template <typename T> struct Solver {
     return mv;
   }
 
+  // ------------------------------------------------------------ Householder QR (line 5, ill-conditioned blocks)
+  // X (n x k, ld ldx) <- Q of X = Q R by blocked Householder QR (panels of 32 reflectors, compact-WY
+  // trailing updates and Q formation through FP64-class products).  Unlike Cholesky-QR it keeps every
+  // direction of X down to rounding, whatever the conditioning (the paper's QR is a Householder geqrf).
+  // Scratch: T1 (reflectors, n x k), T2 (Q), hh (panel factors and products), dwork (tau).
+  void householder_qr(T* X, int64_t n, int k, int64_t ldx) {
+    constexpr int NB = 32;
+    T* Vx = T1();
+    T* Q = T2();
+    T* Tw = (T*)c->hh;               // NB x k: the panels' compact-WY factors
+    T* alpha = Tw + (int64_t)NB * k; // k
+    T* Gv = alpha + k;               // NB x NB
+    T* W1 = Gv + NB * NB;            // NB x k
+    T* W2 = W1 + (int64_t)NB * k;    // NB x k
+    double* tau = c->dwork;
+    for (int j0 = 0; j0 < k; j0 += NB) {
+      const int pb = std::min(NB, k - j0);
+      const int64_t m = n - j0;
+      for (int j = 0; j < pb; ++j) {
+        const int col = j0 + j;
+        T* x = X + col + (int64_t)col * ldx;
+        householder_vec<T>(st(), n - col, x, alpha + col, tau + col);
+        householder_apply<T>(st(), n - col, x, x + ldx, ldx, pb - j - 1, tau + col);
+      }
+      T* Vp = Vx + j0 + (int64_t)j0 * n;  // the panel's reflectors, rows j0.., ld n
+      reflector_panel<T>(st(), m, pb, X + j0 + (int64_t)j0 * ldx, ldx, Vp, n);
+      Epi eg;
+      eg.C = Gv;
+      eg.ldc = pb;
+      gemm(OP_C, Vp, n, OP_N, Vp, n, pb, pb, m, eg, CHASE_FP64);
+      T* Tp = Tw + (int64_t)j0 * NB;
+      householder_T<T>(st(), pb, Gv, tau + j0, Tp, NB);
+      const int rest = k - j0 - pb;
+      if (rest > 0) {
+        // X(j0:, j0+pb:) <- (I - V Tp^H V^H) X(j0:, j0+pb:)
+        T* Xt = X + j0 + (int64_t)(j0 + pb) * ldx;
+        Epi e1;
+        e1.C = W1;
+        e1.ldc = NB;
+        gemm(OP_C, Vp, n, OP_N, Xt, ldx, pb, rest, m, e1, CHASE_FP64);
+        Epi e2;
+        e2.C = W2;
+        e2.ldc = NB;
+        gemm(OP_C, Tp, NB, OP_N, W1, NB, pb, rest, pb, e2, CHASE_FP64);
+        Epi e3;
+        e3.C = Xt;
+        e3.ldc = ldx;
+        e3.alpha = -1.0;
+        e3.Z = Xt;
+        e3.ldz = ldx;
+        e3.beta = 1.0;
+        gemm(OP_N, Vp, n, OP_N, W2, NB, m, rest, pb, e3, CHASE_FP64);
+      }
+    }
+    // Q = H_1 ... H_k [I; 0], panels applied last to first
+    identity_rect<T>(st(), n, k, Q, n);
+    for (int j0 = ((k - 1) / NB) * NB; j0 >= 0; j0 -= NB) {
+      const int pb = std::min(NB, k - j0);
+      const int64_t m = n - j0;
+      const int cols = k - j0;
+      T* Vp = Vx + j0 + (int64_t)j0 * n;
+      T* Tp = Tw + (int64_t)j0 * NB;
+      T* Qt = Q + j0 + (int64_t)j0 * n;
+      Epi e1;
+      e1.C = W1;
+      e1.ldc = NB;
+      gemm(OP_C, Vp, n, OP_N, Qt, n, pb, cols, m, e1, CHASE_FP64);
+      Epi e2;
+      e2.C = W2;
+      e2.ldc = NB;
+      gemm(OP_N, Tp, NB, OP_N, W1, NB, pb, cols, pb, e2, CHASE_FP64);
+      Epi e3;
+      e3.C = Qt;
+      e3.ldc = n;
+      e3.alpha = -1.0;
+      e3.Z = Qt;
+      e3.ldz = n;
+      e3.beta = 1.0;
+      gemm(OP_N, Vp, n, OP_N, W2, NB, m, cols, pb, e3, CHASE_FP64);
+    }
+    copy_cols<T>(st(), n, k, Q, n, X, ldx);
+  }
+
   // ------------------------------------------------------------ Algorithm 1, line 5
   // X (n x k, ld ldx) <- orthonormal basis of span(X) orthogonal to Y (n x l, ld ldy, orthonormal).
   void qr(const T* Y, int64_t ldy, int l, T* X, int64_t ldx, int64_t n, int k, int qr_mode) {
@@ -420,20 +503,19 @@ template <typename T> struct Solver {
     };
     // Cholesky-QR2 with a projection before each pass, so the final basis is orthogonal to the
     // locked columns to rounding even when X was ill-conditioned.  A filtered block can be numerically
-    // rank deficient (a few eigen-directions amplified beyond 1e16 over the rest): the first pass then
-    // finds columns whose remainder after the columns before them is rounding noise.  Those columns
-    // carry no information a QR could recover; they are replaced by fresh seeded random vectors (which
-    // the next filter steps act on like any start vector) and the pass is repeated.
-    bool ok = false;
-    for (int attempt = 0;; ++attempt) {
-      ok = chol_pass(0.0, attempt < 3 ? c->qr_dep : nullptr);
-      if (ok || ndep == 0) break;
-      c->stats.qr_replaced += ndep;
-      fill_dependent_cols<T>(st(), n, k, X, ldx, c->qr_dep + 1, 0x5DEECE66DULL + 7919ULL * (++c->qr_fill_calls));
+    // rank deficient for a Cholesky-QR (eigen-directions amplified beyond about 1e8 over others): the
+    // first pass then finds columns whose remainder after the columns before them is within the
+    // rounding of the Gram matrix.  Such a block goes to the Householder QR, which keeps those
+    // directions down to rounding; its basis is then projected against the locked columns once more and
+    // re-orthonormalised by Cholesky-QR2 (now well conditioned).
+    bool ok = chol_pass(0.0, c->qr_dep);
+    if (!ok && ndep > 0) {
+      c->stats.qr_householder++;
+      householder_qr(X, n, k, ldx);
       project();
       colnorms<T>(st(), n, k, X, ldx, c->dwork);
       scale_cols<T>(st(), n, k, X, ldx, c->dwork, 1);
-      ndep = 0;
+      ok = chol_pass(0.0);
     }
     if (ok) {
       project();
@@ -1062,6 +1144,7 @@ int64_t chase_workspace_bytes(int64_t n_max, int ne_max, chase_dtype dtype, cons
   if (opts) o = *opts;
   int64_t esz = dtype == CHASE_C128 ? 16 : 8;
   int64_t b = 3 * n_max * ne_max * esz + 2 * (int64_t)ne_max * ne_max * esz + work_elems_for(n_max, ne_max, o) * esz;
+  b += (3 * 32 * (int64_t)ne_max + ne_max + 1024) * esz;  // Householder QR scratch
   b += oz::workspace_bytes(n_max, ne_max, dtype == CHASE_C128, o.oz_slices);
   return b;
 }
@@ -1125,6 +1208,7 @@ chase_status chase_create(chase_ctx** out, int64_t n_max, int ne_max, chase_dtyp
     CHASE_CUDA(cudaMalloc(&c->info, sizeof(int)));
     CHASE_CUDA(cudaMalloc(&c->status_dev, 4 * sizeof(int)));
     CHASE_CUDA(cudaMalloc(&c->qr_dep, (size_t)(ne_max + 1) * sizeof(int)));
+    CHASE_CUDA(cudaMalloc(&c->hh, (size_t)(3 * 32 * (size_t)ne_max + ne_max + 1024) * c->esz));
     oz::create(c->ozw, n_max, ne_max, dtype == CHASE_C128, c->opts.oz_slices);
     // workers of batched solves: same sizes and options, one non-blocking stream each
     chase_opts wo = c->opts;
@@ -1159,7 +1243,7 @@ void chase_destroy(chase_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
                   c->lam_locked, c->eigvals, c->lam_sorted, c->bwd, c->bounds, c->deg, c->perm, c->info,
-                  c->status_dev, c->qr_dep, c->a_stage, c->l0_stage};
+                  c->status_dev, c->qr_dep, c->hh, c->a_stage, c->l0_stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   oz::destroy(c->ozw);

@@ -42,10 +42,16 @@ void copy_cols(cudaStream_t st, int64_t n, int k, const T* src, int64_t lds, T* 
 template <typename T>
 void potrf_lower(cudaStream_t st, int k, T* G, int64_t ldg, int* info, T* work, int64_t work_elems,
                  double pivot_floor = 0.0, int* dep = nullptr);
-// Columns j of X (n x k) with depflags[j] != 0 get seeded standard (complex) Gaussian entries.
+// Householder QR building blocks (blas_f64.cu): reflector of a column segment (v over x, alpha, real tau),
+// application of one reflector to ncols columns, the panel's reflectors with explicit zeros, the
+// compact-WY factor Tm of a panel from Gv = V^H V, and Q = [I; 0].
+template <typename T> void householder_vec(cudaStream_t st, int64_t m, T* x, T* alpha, double* tau);
 template <typename T>
-void fill_dependent_cols(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const int* depflags,
-                         unsigned long long seed);
+void householder_apply(cudaStream_t st, int64_t m, const T* v, T* X, int64_t ldx, int ncols, const double* tau);
+template <typename T> void reflector_panel(cudaStream_t st, int64_t m, int pb, const T* Xp, int64_t ldx, T* V, int64_t ldv);
+template <typename T> void householder_T(cudaStream_t st, int pb, const T* Gv, const double* tau, T* Tm, int64_t ldt);
+template <typename T> void identity_rect(cudaStream_t st, int64_t n, int k, T* Q, int64_t ldq);
+
 // X <- X L^{-H} (right solve with the lower Cholesky factor), X n x k.
 template <typename T>
 void trsm_right_lh(cudaStream_t st, int64_t n, int k, T* X, int64_t ldx, const T* L, int64_t ldl, T* work,

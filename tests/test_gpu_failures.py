@@ -45,19 +45,19 @@ def test_maxiter_cap_returns_noconv(pkg):
     s.close()
 
 
-def test_qr_replaces_numerically_dependent_column(pkg):
+def test_qr_householder_for_numerically_dependent_column(pkg):
     """Two columns equal to 1e-13 relative: Cholesky-QR's first pass sees a pivot at rounding level, so
-    that column is replaced by a seeded random vector and the block still gets an orthonormal basis
-    whose span contains every column of X to rounding."""
+    the block goes to the Householder QR and still gets an orthonormal basis whose span contains every
+    column of X to rounding."""
     n, k = 400, 24
     g = np.random.default_rng(21)
     X = g.standard_normal((n, k)) + 1j * g.standard_normal((n, k))
     X[:, 9] = X[:, 4] + 1e-13 * (g.standard_normal(n) + 1j * g.standard_normal(n))
     s = pkg.Chase(n, k, complex_=True)
-    before = s.stats()["qr_replaced"]
+    before = s.stats()["qr_householder"]
     Xt = dev(X)
     s.qr(Xt)
-    assert s.stats()["qr_replaced"] >= before + 1
+    assert s.stats()["qr_householder"] >= before + 1
     Q = host(Xt)
     assert np.max(np.abs(np.conj(Q.T) @ Q - np.eye(k))) <= 1e-12
     # every column of X lies in span(Q)
@@ -67,7 +67,7 @@ def test_qr_replaces_numerically_dependent_column(pkg):
 
 
 def test_solve_with_near_duplicate_start_columns(pkg):
-    """A start block with two nearly equal columns: the first QR replaces the dependent one and the solve
+    """A start block with two nearly equal columns: the first QR goes to the Householder QR and the solve
     still converges to the oracle's eigenvalues (or reports CHASE_ERR_QR_BREAKDOWN, never a wrong
     result)."""
     p = G.problem_small(300, 10, 6, complex_=True, seed_pid=6)
@@ -82,7 +82,7 @@ def test_solve_with_near_duplicate_start_columns(pkg):
     except pkg.ChaseError as e:
         assert e.status == 4
         return
-    assert s.stats()["qr_replaced"] >= 1
+    assert s.stats()["qr_householder"] >= 1
     assert np.max(np.abs(w.cpu().numpy() - ref.eigvals)) <= 1e-10 * p.norm2()
     V = host(Vt)
     R = A @ V - V * w.cpu().numpy()[None, :]
