@@ -349,7 +349,9 @@ def batched_timing(pkg, np, torch, dev, workers, nprob=64, steps=4, ws=1, rank=0
                # summed over problems (each on its own stream, overlapping one another)
                "filter_gpu_ms": round(ctx.stats()["ms_filter"], 1),
                "stage_ms_sum": {k: round(sum(st[k] for st in stats), 1) for k in ("ms_lanczos", "ms_qr", "ms_rr",
-                                                                                 "ms_resid")}}
+                                                                                 "ms_resid")},
+               "rr_sweeps": int(sum(st["rr_sweeps"] for st in stats)),
+               "iterations_sum": int(sum(st["iterations"] for st in stats))}
         if step == 0:  # exact spectrum known before the first perturbation
             rec["max_abs_eig_err_vs_exact"] = float(max(np.max(np.abs(w.cpu().numpy() - p.lam[:p.nev])) for w, p in
                                                         zip(wvals, probs)))
@@ -393,7 +395,7 @@ def run_batched_only(args):
         for k in tot:
             tot[k] += st[k]
         rows.append({"n": p.n, "ne": p.ne, "wall_ms": round(1e3 * wall, 1), "iterations": st["iterations"],
-                     "matvecs": st["matvecs"], **{k[3:]: round(st[k], 1) for k in tot}})
+                     "matvecs": st["matvecs"], "rr_sweeps": st["rr_sweeps"], **{k[3:]: round(st[k], 1) for k in tot}})
         del At
     ctx.close()
     flops = sum(8.0 * r["n"] ** 2 * r["matvecs"] for r in rows)

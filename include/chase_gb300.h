@@ -98,6 +98,8 @@ typedef struct {
                                    went to the Householder QR */
   int filter_reorth;            /* orthonormalisations inside equal-degree filters whose amplification
                                    would exceed 1e7 (the filtered span is unchanged) */
+  int rr_sweeps;                /* Jacobi sweeps of the Rayleigh-Ritz eigensolves (FP32 first passes and
+                                   FP64 solves) */
 } chase_stats_t;
 
 /* Kernel launches made by this library in this process so far (all contexts). */

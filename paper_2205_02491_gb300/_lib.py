@@ -40,7 +40,8 @@ class Stats(C.Structure):
                 ("ms_filter_kernel", C.c_double), ("filter_kernel_launches", C.c_int),
                 ("ms_filter_kernel_lowp", C.c_double), ("ms_backward", C.c_double),
                 ("minres_iterations", C.c_int), ("rr_clusters", C.c_int), ("rr_fallbacks", C.c_int),
-                ("qr_householder", C.c_int), ("filter_reorth", C.c_int)]
+                ("qr_householder", C.c_int), ("filter_reorth", C.c_int),
+                ("rr_sweeps", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

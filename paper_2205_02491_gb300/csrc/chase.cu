@@ -85,6 +85,7 @@ struct chase_ctx {
   std::vector<chase_ctx*> workers;
   // grouped batched solves: one context per problem (sized to it, own stream), kept between calls
   std::vector<chase_ctx*> slots;
+  cudaStream_t filter_stream = nullptr;  // lowest-priority stream of the grouped filter launches
 };
 
 namespace {
@@ -600,7 +601,8 @@ template <typename T> struct Solver {
     dbg_finite(G, k, k, k, sizeof(T), "G before the FP32 pass");
     convert_mat<T, F>(st(), k, G, k, Gf, k);
     try {
-      heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40, false, true);
+      c->stats.rr_sweeps += heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40, false,
+                                           true);
     } catch (const Error& e) {
       // non-finite FP32 values: G itself is untouched and the FP64 solver takes over; a grid barrier
       // that hit its wait limit is reported as CHASE_ERR_TIMEOUT
@@ -695,7 +697,7 @@ template <typename T> struct Solver {
     }
     if (!done) {
       T* jw = (T*)c->work;  // Jacobi workspace (k*k + 3k + 8 scalars)
-      heev_jacobi<T>(st(), k, Gb(), k, ritz, Zb(), k, jw, c->work_elems, c->dwork, c->iwork, 1e-14, 60);
+      c->stats.rr_sweeps += heev_jacobi<T>(st(), k, Gb(), k, ritz, Zb(), k, jw, c->work_elems, c->dwork, c->iwork, 1e-14, 60);
     }
     Epi v;
     v.C = Tv;
@@ -1239,6 +1241,11 @@ void chase_destroy(chase_ctx* c) {
   c->workers.clear();
   for (chase_ctx* w : c->slots) chase_destroy(w);
   c->slots.clear();
+  if (c->filter_stream) {
+    cudaStreamSynchronize(c->filter_stream);
+    cudaStreamDestroy(c->filter_stream);
+    c->filter_stream = nullptr;
+  }
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   void* ptrs[] = {c->V, c->T1, c->T2, c->G, c->Z, c->work, c->dwork, c->iwork, c->ritz, c->res, c->ritz2, c->res2,
@@ -1547,8 +1554,12 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
       sl = nullptr;
     }
     if (!sl) {
+      // the problems' streams get the highest priority: their short, latency-bound QR / Rayleigh-Ritz
+      // kernels take SMs as soon as blocks of the grouped filter (lowest priority) finish
+      int least = 0, greatest = 0;
+      CHASE_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
       cudaStream_t ws = nullptr;
-      CHASE_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+      CHASE_CUDA(cudaStreamCreateWithPriority(&ws, cudaStreamNonBlocking, greatest));
       chase_status st = chase_create(&sl, n[p], ne, c->dtype, &so, ws);
       if (st != CHASE_OK) {
         cudaStreamDestroy(ws);
@@ -1558,6 +1569,12 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
       sl->own_stream = true;
     }
   }
+  if (!c->filter_stream) {
+    int least = 0, greatest = 0;
+    CHASE_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CHASE_CUDA(cudaStreamCreateWithPriority(&c->filter_stream, cudaStreamNonBlocking, least));
+  }
+  cudaStream_t fs = c->filter_stream;
   // inputs the caller enqueued on the batch context's stream must be complete before the problem streams
   CHASE_CUDA(cudaStreamSynchronize(c->stream));
   std::vector<typename Solver<T>::Run> R(nprob);
@@ -1632,7 +1649,7 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
       ++R[p].it;
       cudaEvent_t e = event(cudaEventDisableTiming);
       CHASE_CUDA(cudaEventRecord(e, sc->stream));
-      CHASE_CUDA(cudaStreamWaitEvent(c->stream, e, 0));
+      CHASE_CUDA(cudaStreamWaitEvent(fs, e, 0));
       if (R[p].k() <= 0) continue;
       FilterPlan fp;
       fp.p = p;
@@ -1642,9 +1659,9 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
       smax = std::max(smax, mmax);
       plans.push_back(std::move(fp));
     }
-    CHASE_CUDA(cudaEventRecord(t0, c->stream));
+    CHASE_CUDA(cudaEventRecord(t0, fs));
     // the digit planes of A: computed once per solve (cached in the problem's workspace)
-    for (FilterPlan& fp : plans) oz::prepare_A<T>(c->stream, c->slots[fp.p]->ozw, R[fp.p].A, R[fp.p].n, R[fp.p].lda,
+    for (FilterPlan& fp : plans) oz::prepare_A<T>(fs, c->slots[fp.p]->ozw, R[fp.p].A, R[fp.p].n, R[fp.p].lda,
                                                   CHASE_FP64);
     std::vector<oz::ProductOp> ops_hi, ops_lo;
     for (int sstep = 1; sstep <= smax; ++sstep) {
@@ -1664,7 +1681,7 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
         T* out = Bb[sstep & 1] + (int64_t)fp.f * r.n;
         const T* in = Bb[(sstep - 1) & 1] + (int64_t)fp.f * r.n;
         const int fmode = r.fmode();
-        oz::split_right<T>(c->stream, sc->ozw, fmode, in, r.n, cols, r.n);
+        oz::split_right<T>(fs, sc->ozw, fmode, in, r.n, cols, r.n);
         Epi e;
         e.C = out;
         e.ldc = r.n;
@@ -1682,9 +1699,9 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
         (fmode == CHASE_FP64 ? ops_hi : ops_lo).push_back(op);
         sc->stats.filter_launches++;
       }
-      if (!ops_hi.empty()) oz::launch_group<CPLX>(c->stream, c->ozw, CHASE_FP64, ops_hi.data(), (int)ops_hi.size());
+      if (!ops_hi.empty()) oz::launch_group<CPLX>(fs, c->ozw, CHASE_FP64, ops_hi.data(), (int)ops_hi.size());
       // the low-precision problems of one batch share its mode
-      if (!ops_lo.empty()) oz::launch_group<CPLX>(c->stream, c->ozw, mode, ops_lo.data(), (int)ops_lo.size());
+      if (!ops_lo.empty()) oz::launch_group<CPLX>(fs, c->ozw, mode, ops_lo.data(), (int)ops_lo.size());
     }
     for (FilterPlan& fp : plans) {
       auto& r = R[fp.p];
@@ -1693,14 +1710,14 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
       T* Vact = (T*)sc->V + (int64_t)r.l * r.n;
       T* T1act = (T*)sc->T1 + (int64_t)r.l * r.n;
       dim3 grid(std::min<unsigned>(ceil_div(r.n, 256), 64), k);
-      gather_odd_kernel<T><<<grid, 256, 0, c->stream>>>(r.n, sc->deg, Vact, r.n, T1act, r.n);
+      gather_odd_kernel<T><<<grid, 256, 0, fs>>>(r.n, sc->deg, Vact, r.n, T1act, r.n);
       CHASE_CHECK_LAUNCH();
       Solver<T>(sc).count_matvecs(r, fp.mv);
     }
-    CHASE_CUDA(cudaEventRecord(t1, c->stream));
+    CHASE_CUDA(cudaEventRecord(t1, fs));
     filter_times.emplace_back(t0, t1);
     cudaEvent_t done_f = event(cudaEventDisableTiming);
-    CHASE_CUDA(cudaEventRecord(done_f, c->stream));
+    CHASE_CUDA(cudaEventRecord(done_f, fs));
     for (int p : active) CHASE_CUDA(cudaStreamWaitEvent(c->slots[p]->stream, done_f, 0));
   };
   // lines 5-14 per problem of a cohort, on the host threads (each problem on its own stream)
@@ -1726,16 +1743,16 @@ static void solve_batched_grouped(chase_ctx* c, int nprob, const void* const* A,
       act[h] = active_of(h);
       if (!act[h].empty()) enqueue_filter(act[h]);
     }
-    CHASE_CUDA(cudaStreamSynchronize(c->stream));
+    CHASE_CUDA(cudaStreamSynchronize(fs));
     for (auto& t : filter_times) {
       float ms = 0.f;
       CHASE_CUDA(cudaEventElapsedTime(&ms, t.first, t.second));
       c->stats.ms_filter += ms;
     }
-    CHASE_REQUIRE(oz::read_flags(c->stream, c->ozw) == 0, CHASE_ERR_TIMEOUT,
+    CHASE_REQUIRE(oz::read_flags(fs, c->ozw) == 0, CHASE_ERR_TIMEOUT,
                   "a grouped tensor-core product hit its wait limit");
   } catch (...) {
-    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(fs);
     for (cudaEvent_t e : evs) cudaEventDestroy(e);
     throw;
   }
