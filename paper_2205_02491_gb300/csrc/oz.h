@@ -40,6 +40,8 @@ struct Workspace {
   double* l_scale = nullptr;  // per-row scale of the general left operand
   double* b_scale = nullptr;  // per-column scale of the right operand
   int* flags = nullptr;       // device error flags of the bounded waits
+  double* partial = nullptr;  // FP64 partial sums of products split along K
+  int64_t partial_elems = 0;
   int group_m = 8;            // row blocks per tile group of the split-product launch order (untuned launches)
   bool autotune = true;       // choose LaunchCfg per size class by timing the candidates
   std::map<uint64_t, TuneEntry> tune;  // size class -> measurements and choice
@@ -63,6 +65,9 @@ struct ProductOp {
   int64_t M, N, K;
   Epi e;
   int group_m;
+  int ksplit = 1;           // K slices (> 1: partial sums to `part`, then a reduction launch)
+  int klen = 0;             // slice length along K (multiple of 96)
+  double* part = nullptr;   // ksplit x M x N (x 2 complex) doubles
 };
 
 bool available();

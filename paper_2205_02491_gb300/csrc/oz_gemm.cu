@@ -271,13 +271,17 @@ struct EpiArgs {
 // sizes, scales and epilogue.  The launch's tiles are the problems' tiles back to back: problem p owns
 // blocks [tile_begin[p], tile_begin[p + 1]).  Passed as one __grid_constant__ parameter (the tensor maps
 // must live in parameter, constant or global memory for TMA); G = 64 is about 24 KB.
+// A product may also be split along K into ksplit slices of klen (a multiple of 96) for launches with
+// few output tiles: each slice's CTA writes its FP64 partial sum to part (slice-major, column-major
+// M x N, re/im interleaved for complex) and split_reduce_kernel adds the slices and applies the epilogue.
 template <int G> struct GroupParams {
   CUtensorMap tmA[G];
   CUtensorMap tmB[G];
   EpiArgs ep[G];
   const double* a_scale[G];
   const double* b_scale[G];
-  int M[G], N[G], K[G], group_m[G];
+  double* part[G];
+  int M[G], N[G], K[G], group_m[G], ksplit[G], klen[G];
   int tile_begin[G + 1];
   int nprob;
 };
@@ -299,8 +303,10 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
   const EpiArgs& ep = gp.ep[prob];
   const double* __restrict__ a_scale = gp.a_scale[prob];
   const double* __restrict__ b_scale = gp.b_scale[prob];
-  const int M = gp.M[prob], N = gp.N[prob], K = gp.K[prob], group_m = gp.group_m[prob];
-  const int local_tile = (int)blockIdx.x - gp.tile_begin[prob];
+  const int M = gp.M[prob], N = gp.N[prob], group_m = gp.group_m[prob];
+  const int ksplit = gp.ksplit[prob];
+  double* __restrict__ part_out = gp.part[prob];
+  int local_tile = (int)blockIdx.x - gp.tile_begin[prob];
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = smem;
@@ -321,6 +327,11 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
   if (*(volatile int*)err != 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int num_m = (M + BM - 1) / BM, num_n = (N + Cf::NCOLS - 1) / Cf::NCOLS;
+  // K slice of this block (slice-major tile order; one slice unless the product is split along K)
+  const int kslice = local_tile / (num_m * num_n);
+  local_tile -= kslice * num_m * num_n;
+  const int kbeg = kslice * gp.klen[prob];
+  const int K = min(gp.K[prob] - kbeg, gp.klen[prob]);  // this slice's extent along K
   const int per_group = group_m * num_n;
   const int first_m = (local_tile / per_group) * group_m;
   const int gm = min(group_m, num_m - first_m);
@@ -361,7 +372,7 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
     int a_iter = 0, b_issued = 0;
     bool ok = true;
     for (int kb = 0; kb < nkb && ok; ++kb) {
-      const int k0 = kb * BK;
+      const int k0 = kbeg + kb * BK;
       const int bs = kb % B_STAGES;
       if (!mbar_wait(smem_u32(&b_empty[bs]), ((kb / B_STAGES) & 1) ^ 1, abort_sh, err)) {
         ok = false;
@@ -570,6 +581,10 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
           if (NEX > 0) v += (double)acc64[NEX > 0 ? j : 0] * 2.3283064365386963e-10;  // 2^-32
           v *= rs * b_scale[gj] * 6.103515625e-05;                                   // 2^-14
           const int comp = CPLX ? 2 : 1;
+          if (ksplit > 1) {
+            part_out[(((int64_t)kslice * N + gj) * M + gi) * comp + part] = v;
+            continue;
+          }
           double out = ep.alpha * v;
           if (ep.Y) {
             const double g = ep.gamma * (ep.ycol ? ep.ycol[gj] : 1.0);
@@ -585,6 +600,28 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
   __syncthreads();
   fence_after();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cf::TMEM_COLS));
+}
+
+// C = alpha sum_s part[s] + gamma ycol Y + beta Z over the ksplit K slices (slice order fixed, so the
+// result does not depend on scheduling).
+template <bool CPLX>
+__global__ void split_reduce_kernel(int M, int N, int ksplit, const double* __restrict__ part, EpiArgs ep) {
+  constexpr int comp = CPLX ? 2 : 1;
+  const int64_t total = (int64_t)M * N * comp;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int pt = (int)(idx % comp);
+    const int64_t e = idx / comp;
+    const int gi = (int)(e % M), gj = (int)(e / M);
+    double v = 0.0;
+    for (int ks = 0; ks < ksplit; ++ks) v += part[(int64_t)ks * total + idx];
+    double out = ep.alpha * v;
+    if (ep.Y) {
+      const double g = ep.gamma * (ep.ycol ? ep.ycol[gj] : 1.0);
+      out += g * ((const double*)ep.Y)[(gi + (int64_t)gj * ep.ldy) * comp + pt];
+    }
+    if (ep.Z) out += ep.beta * ((const double*)ep.Z)[(gi + (int64_t)gj * ep.ldz) * comp + pt];
+    ((double*)ep.C)[(gi + (int64_t)gj * ep.ldc) * comp + pt] = out;
+  }
 }
 
 // ---------------------------------------------------------------- split kernels
@@ -773,7 +810,7 @@ int64_t workspace_bytes(int64_t n_max, int ne_max, bool complex_, int slices) {
   int64_t a = (int64_t)slices * ap * n_max * kp * 2;
   int64_t l = (int64_t)slices * ap * left_elems(n_max, ne_max) * 2;
   int64_t b = (int64_t)slices * bp * ne_max * kp * 2;
-  return a + l + b + (2 * n_max + 2 * ne_max) * 8 + 64;
+  return a + l + b + (2 * n_max + 2 * ne_max) * 8 + 64 + (8ll << 20) * 8;
 }
 
 void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices) {
@@ -792,11 +829,14 @@ void create(Workspace& w, int64_t n_max, int ne_max, bool complex_, int slices) 
   CHASE_CUDA(cudaMalloc(&w.b_scale, ne_max * sizeof(double)));
   CHASE_CUDA(cudaMalloc(&w.flags, 16 * sizeof(int)));
   CHASE_CUDA(cudaMemset(w.flags, 0, 16 * sizeof(int)));
+  // partial sums of K-split products: up to about 4 waves of 128 x 40 complex tiles
+  w.partial_elems = 8ll << 20;
+  CHASE_CUDA(cudaMalloc(&w.partial, (size_t)w.partial_elems * sizeof(double)));
   w.ready = true;
 }
 
 void destroy(Workspace& w) {
-  void* ps[] = {w.a_planes, w.l_planes, w.b_planes, w.a_scale, w.l_scale, w.b_scale, w.flags};
+  void* ps[] = {w.a_planes, w.l_planes, w.b_planes, w.a_scale, w.l_scale, w.b_scale, w.flags, w.partial};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& e : w.ev) cudaEventDestroy(e);
@@ -983,8 +1023,11 @@ static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int 
     gp.N[q] = (int)o.N;
     gp.K[q] = (int)o.K;
     gp.group_m[q] = std::max(1, o.group_m);
+    gp.ksplit[q] = std::max(1, o.ksplit);
+    gp.klen[q] = o.ksplit > 1 ? o.klen : (int)o.K;
+    gp.part[q] = o.part;
     gp.tile_begin[q] = (int)tiles;
-    tiles += (int64_t)ceil_div(o.N, Cf::NCOLS) * (int64_t)ceil_div(o.M, BM);
+    tiles += (int64_t)ceil_div(o.N, Cf::NCOLS) * (int64_t)ceil_div(o.M, BM) * gp.ksplit[q];
     CHASE_REQUIRE(tiles <= 0x7fffffff, 1, "split product: too many tiles");
   }
   gp.tile_begin[nops] = (int)tiles;
@@ -1003,10 +1046,47 @@ static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int 
   if (tune_ev) CHASE_CUDA(cudaEventRecord(tune_ev[0], st));
   oz_gemm_kernel<S, NEX, CPLX, NTT, G><<<(unsigned)tiles, NTHREADS, Cf::SMEM_BYTES, st>>>(gp, w.flags);
   CHASE_CHECK_LAUNCH();
+  for (int q = 0; q < nops; ++q) {
+    if (gp.ksplit[q] <= 1) continue;
+    const int64_t total = ops[q].M * ops[q].N * (CPLX ? 2 : 1);
+    split_reduce_kernel<CPLX><<<(unsigned)std::min<int64_t>(ceil_div(total, 256), 4096), 256, 0, st>>>(
+        (int)ops[q].M, (int)ops[q].N, gp.ksplit[q], ops[q].part, gp.ep[q]);
+    CHASE_CHECK_LAUNCH();
+  }
   if (tune_ev) CHASE_CUDA(cudaEventRecord(tune_ev[1], st));
   if (timed) {
     CHASE_CUDA(cudaEventRecord(w.ev[w.ev_used + 1], st));
     w.ev_used += 2;
+  }
+}
+
+static int sm_count() {
+  static const int n = []() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 148;
+    return sms;
+  }();
+  return n;
+}
+
+// A product with fewer output tiles than two per SM is split along K (slices of at least 384, multiples of
+// 96, at most 16 of them, within the partial-sum buffer) so that its launch covers the GPU.
+static void plan_ksplit(Workspace& w, ProductOp& op, int ncols_tile, bool cplx) {
+  const int64_t tiles = (int64_t)ceil_div(op.N, ncols_tile) * (int64_t)ceil_div(op.M, BM);
+  const int64_t want = 2 * (int64_t)sm_count();
+  if (tiles >= want || op.K < 2 * 384 || !w.partial) return;
+  int64_t ks = std::min<int64_t>({16, ceil_div(want, tiles), op.K / 384});
+  const int64_t per = op.M * op.N * (cplx ? 2 : 1);
+  ks = std::min<int64_t>(ks, w.partial_elems / std::max<int64_t>(1, per));
+  if (ks <= 1) return;
+  const int64_t klen = ((op.K + ks - 1) / ks + 95) / 96 * 96;
+  op.klen = (int)klen;
+  op.ksplit = (int)ceil_div(op.K, klen);
+  op.part = w.partial;
+  if (op.ksplit <= 1) {
+    op.ksplit = 1;
+    op.part = nullptr;
   }
 }
 
@@ -1015,6 +1095,7 @@ static void launch(cudaStream_t st, Workspace& w, const void* lpl, const double*
                    const void* rpl, const double* rsc, int64_t M, int64_t N, int64_t K, const Epi& e,
                    int group_m, cudaEvent_t* tune_ev) {
   ProductOp op{lpl, lsc, l_slices_total, rpl, rsc, M, N, K, e, group_m};
+  plan_ksplit(w, op, Cfg<S, NEX, CPLX, NTT>::NCOLS, CPLX);
   launch_ops<S, NEX, CPLX, NTT, 1>(st, w, &op, 1, tune_ev);
 }
 

@@ -45,6 +45,26 @@ def test_hemm_fp64_split_complex(pkg, n, k):
     assert _rel_err(C, ref, A, B) <= 2.0 ** -53
 
 
+@pytest.mark.parametrize("cplx,n,k", [(True, 4096, 16), (True, 5000, 6), (False, 3000, 8), (False, 2500, 70)])
+def test_hemm_split_along_k(pkg, cplx, n, k):
+    """Products with few output tiles are split along K (FP64 partial sums per slice, then one reduction);
+    the narrow Lanczos-width case (up to 8 complex / 16 real columns) takes the 16-column tile.  Same
+    per-term bound as the unsplit products."""
+    p = G.problem_small(n, 2, 2, complex_=cplx, seed_pid=n + 3)
+    A = p.dense()
+    B = G.gaussian(np.random.default_rng(n + 1), (n, k), cplx)
+    s = pkg.Chase(n, max(k, 4), complex_=cplx)
+    C = host(s.hemm(dev(A), dev(B), "fp64"))
+    if cplx:
+        ref = _exact(A, B)
+        assert _rel_err(C, ref, A, B) <= 2.0 ** -53
+    else:
+        ref = (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
+        ra = np.max(np.abs(A), axis=1)
+        cb = np.max(np.abs(B), axis=0)
+        assert np.max(np.abs(C - ref) / (ra[:, None] * cb[None, :])) / n <= 2.0 ** -53
+
+
 @pytest.mark.parametrize("n,k", [(257, 200), (64, 3)])
 def test_hemm_fp64_split_real(pkg, n, k):
     p = G.problem_small(n, 2, 2, complex_=False, seed_pid=n + 2)
