@@ -68,7 +68,10 @@ template <int S, int NEX, bool CPLX, int NTT> struct Cfg {
   static constexpr int B_STAGE = (B_BYTES + 1023) / 1024 * 1024;  // stage stride (1 KB aligned)
   static constexpr int SMEM_LIMIT = 232448 - 1024 - 256;
   static constexpr int A_FIT = (SMEM_LIMIT - B_STAGES * B_STAGE) / A_SLOT;
-  static constexpr int A_SLOTS = A_FIT < 8 ? A_FIT : 8;  // ring of left-operand slices (>= S)
+  // ring of left-operand slices (>= S): as deep as shared memory allows, at most 12 (the barrier area
+  // holds 2 x 12 + 2 x B_STAGES + 3 mbarriers plus two words); narrow tiles, whose MMAs are short, need
+  // the extra depth to keep the copies of the next k-block in flight
+  static constexpr int A_SLOTS = A_FIT < 12 ? A_FIT : 12;
   static constexpr int NACC = NEX + 1;
   static constexpr int TMEM_USED = NACC * NT;
   static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : (TMEM_USED <= 256 ? 256 : 512);
@@ -79,6 +82,7 @@ template <int S, int NEX, bool CPLX, int NTT> struct Cfg {
   static_assert(TMEM_USED <= 512, "TMEM");
   static_assert(SMEM_BYTES <= 232448, "shared memory");
   static_assert(A_SLOTS >= S, "a k-block's slices must fit in the ring");
+  static_assert((2 * A_SLOTS + 2 * B_STAGES + 3) * 8 + 8 <= 256, "barrier area");
   static_assert(EPI_COLS % 8 == 0, "epilogue loads 8 columns at a time");
 };
 
