@@ -384,10 +384,9 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
       }
       ++b_issued;
       mbar_expect_tx(smem_u32(&b_full[bs]), Cf::B_BYTES);
-      for (int u = 0; u < S; ++u)
-        for (int p = 0; p < Cf::BP; ++p)
-          tma_load_3d(smem_u32(sB + bs * Cf::B_STAGE + u * Cf::B_SLICE + p * Cf::B_PLANE), &tmB,
-                      smem_u32(&b_full[bs]), k0, n0, u * Cf::BP + p);
+      // every slice and plane of the right operand's k-block in one copy (the box spans all S x BP planes,
+      // landing plane-major exactly as the MMA descriptors expect)
+      tma_load_3d(smem_u32(sB + bs * Cf::B_STAGE), &tmB, smem_u32(&b_full[bs]), k0, n0, 0);
       for (int ti = 0; ti < S; ++ti, ++a_iter) {
         const int t = S - 1 - ti;
         const int as = a_iter % Cf::A_SLOTS;
@@ -396,9 +395,8 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
           break;
         }
         mbar_expect_tx(smem_u32(&a_full[as]), Cf::A_SLOT);
-        for (int p = 0; p < Cf::AP; ++p)
-          tma_load_3d(smem_u32(sA + as * Cf::A_SLOT + p * Cf::A_PLANE), &tmA, smem_u32(&a_full[as]), k0, m0,
-                      t * Cf::AP + p);
+        // both planes (re, im) of the slice in one copy
+        tma_load_3d(smem_u32(sA + as * Cf::A_SLOT), &tmA, smem_u32(&a_full[as]), k0, m0, t * Cf::AP);
       }
     }
     // drain: every issued copy must have landed before the CTA exits
@@ -769,11 +767,13 @@ static EncodeFn encode_fn() {
   return fn;
 }
 
-static CUtensorMap make_map(const void* base, int64_t K, int64_t Kpad, int64_t rows, int planes, int box_rows) {
+// box: BK (K) x box_rows x box_planes consecutive planes; a copy lands plane-major in shared memory
+static CUtensorMap make_map(const void* base, int64_t K, int64_t Kpad, int64_t rows, int planes, int box_rows,
+                            int box_planes) {
   CUtensorMap m;
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)(Kpad * 2), (cuuint64_t)(Kpad * 2 * rows)};
-  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
   cuuint32_t es[3] = {1, 1, 1};
   EncodeFn fn = encode_fn();
   CHASE_REQUIRE(fn != nullptr, 9, "cuTensorMapEncodeTiled unavailable");
@@ -1017,8 +1017,8 @@ static void launch_ops(cudaStream_t st, Workspace& w, const ProductOp* ops, int 
   for (int q = 0; q < nops; ++q) {
     const ProductOp& o = ops[q];
     const int64_t kp = kpad(o.K);
-    gp.tmA[q] = make_map(o.lpl, o.K, kp, o.M, o.l_slices_total * ap, BM);
-    gp.tmB[q] = make_map(o.rpl, o.K, kp, o.N, S * bp, Cf::BROWS);
+    gp.tmA[q] = make_map(o.lpl, o.K, kp, o.M, o.l_slices_total * ap, BM, ap);
+    gp.tmB[q] = make_map(o.rpl, o.K, kp, o.N, S * bp, Cf::BROWS, S * bp);
     const Epi& e = o.e;
     gp.ep[q] = EpiArgs{e.C, e.ldc, e.alpha, e.Y, e.ldy, e.gamma, e.ycol, e.Z, e.ldz, e.beta};
     gp.a_scale[q] = o.lsc;
