@@ -160,10 +160,12 @@ class Clocks:
 
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one full-width filter launch of the
-# current kernel, captured at n = 8192 with 1600 columns (one launch, --clock-control none) and scaled to
-# the bench's n by (n / 8192)^2: the A planes are read once per launch and the right-operand planes once
-# per row block of tiles, both proportional to n^2 at a fixed column count.  None until captured.
-FILTER_TRAFFIC_N8192 = None
+# current kernel, captured at n = 8192 with 1600 columns (`bench.py --hemm-only fp64 --n 8192`, one launch,
+# --clock-control none; profiles/oz_gemm_fp64_complex_n8192.md): 24.387 GB read + 0.760 GB written.  Scaled
+# to the bench's n by (n / 8192)^2: at a fixed column count the launch has n / 128 row blocks, each streaming
+# planes of length n, so both the left- and the right-operand traffic grow as n^2.  Set to None when the
+# kernel changes until it is captured again.
+FILTER_TRAFFIC_N8192 = 25.147e9
 
 
 def filter_traffic_bytes(n, ne, slices):

@@ -226,9 +226,11 @@ template <typename T> struct Solver {
     double mflop = (S<T>::cplx ? 8.0 : 2.0) * (double)M * (double)N * (double)K * 1e-6;
     return mflop >= (double)c->opts.native_below_mflop;
   }
+  // force_split: the split tensor-core product whatever the size (for the skinny products of a long loop,
+  // which split along K where DFMA tiles stay latency-bound)
   void gemm(Op opA, const T* A, int64_t lda, Op opB, const T* B, int64_t ldb, int64_t M, int64_t N, int64_t K,
-            const Epi& e, int mode) {
-    if (use_split(mode, M, N, K))
+            const Epi& e, int mode, bool force_split = false) {
+    if ((force_split && mode != CHASE_FP64_NATIVE && oz::available()) || use_split(mode, M, N, K))
       oz::gemm<T>(st(), c->ozw, opA, A, lda, opB, B, ldb, M, N, K, e, CHASE_FP64);
     else
       gemm_f64<T>(st(), opA, opB, M, N, K, A, lda, B, ldb, e, W(), c->work_elems);
@@ -779,7 +781,7 @@ template <typename T> struct Solver {
         Epi ep;
         ep.C = Mp;
         ep.ldc = l;
-        gemm(OP_C, Vs, n, OP_N, Yb, n, l, nev, n, ep, CHASE_FP64);
+        gemm(OP_C, Vs, n, OP_N, Yb, n, l, nev, n, ep, CHASE_FP64, true);
         Epi eu;
         eu.C = Yb;
         eu.ldc = n;
@@ -787,7 +789,7 @@ template <typename T> struct Solver {
         eu.Z = Yb;
         eu.ldz = n;
         eu.beta = 1.0;
-        gemm(OP_N, Vs, n, OP_N, Mp, l, n, nev, l, eu, CHASE_FP64);  // Y -= V_S (V_S^T Y)
+        gemm(OP_N, Vs, n, OP_N, Mp, l, n, nev, l, eu, CHASE_FP64, true);  // Y -= V_S (V_S^T Y)
         minres_update(st(), n, nev, (const double*)Yb, (double*)r1, (const double*)r2, (double*)Vv, (double*)wn,
                       (const double*)wc, (double*)X, state, tol);
         std::swap(r1, r2);
