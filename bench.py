@@ -541,6 +541,7 @@ def run_ours(args):
         ctx = pkg.Chase(n, ne, complex_=True, opts={"maxiter": 1})
         torch.cuda.synchronize()
         e_fl, e_ms = 0.0, 0.0
+        e_stage = {k: 0.0 for k in ("ms_total", "ms_lanczos", "ms_filter", "ms_qr", "ms_rr", "ms_resid")}
         h2d = (A_host.numel() + V0h.numel() + L0h.numel()) * 16
         d2h = 6 * 8 + 4 * ne + 8 * ne + 8 * ne + 4
         for it in range(args.steps + 1):
@@ -558,8 +559,11 @@ def run_ours(args):
             if it > 0:  # the first pass allocates the library's device copy of A
                 e_ms += e0.elapsed_time(e1)
                 e_fl += 8.0 * n * n * st["matvecs"]
+                for k in e_stage:
+                    e_stage[k] += st[k] / args.steps
         e2e = {"value": ws * e_fl / (e_ms * 1e-3) / 1e12, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms / args.steps,
+               "stage_ms": {k: round(v, 1) for k, v in e_stage.items()},
                "note": "filter flops over the whole step, chase_solve called with pinned host buffers (the "
                        "library's host-to-device copies inside the timed region)"}
         ctx.close()

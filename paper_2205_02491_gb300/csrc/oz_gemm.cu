@@ -191,6 +191,12 @@ __device__ __forceinline__ void mma_bf16_c(uint32_t tmem_d, uint64_t adesc, uint
     mma_bf16(tmem_d, adesc, bdesc, idesc, acc);
 }
 
+// collector hint COL as above; EN: enable_input_d as a compile-time constant (0 starts the accumulator)
+template <int COL, int EN>
+__device__ __forceinline__ void mma_bf16_ce(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+  mma_bf16_c<COL>(tmem_d, adesc, bdesc, idesc, (uint32_t)EN);
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -267,6 +273,35 @@ struct EpiArgs {
   int64_t ldz;
   double beta;
 };
+
+// Accumulator of digit level L: levels below NEX have their own (exact) accumulators, the rest share one.
+__host__ __device__ constexpr int acc_of(int level, int nex) { return level < nex ? level : nex; }
+
+// Issue order of one k-block's MMAs: slices t descending; per slice the left planes pl, the two K-steps ks
+// and the right slices u descending over the pass's range (pass 0: all pairs; 1: inexact levels; 2: exact
+// levels).  An MMA starts its accumulator (enable_input_d = 0) when it is the accumulator's first MMA in
+// that order and the k-block restarts it: mode 0 = the first k-block (every accumulator), mode 1 = the
+// first k-block of a later chunk (exact accumulators, whose first MMAs are in pass 2), mode 2 = neither.
+// Evaluated on compile-time arguments only, so the issuer's per-MMA enable flags are constants.
+template <int S, int NEX, int AP>
+__host__ __device__ constexpr bool first_touch(int t, int pl, int ks, int u, int pass, int mode) {
+  if (mode == 2) return false;
+  const int a = acc_of(t + u, NEX);
+  if (mode == 1 && a >= NEX) return false;
+  for (int ti = 0; ti < S; ++ti) {
+    const int tt = S - 1 - ti;
+    int ulo = 0, uhi = S - 1 - tt;
+    if (pass == 1) ulo = NEX - tt > 0 ? NEX - tt : 0;
+    if (pass == 2 && NEX - 1 - tt < uhi) uhi = NEX - 1 - tt;
+    for (int p = 0; p < AP; ++p)
+      for (int k = 0; k < BK / 16; ++k)
+        for (int uu = uhi; uu >= ulo; --uu) {
+          if (tt == t && p == pl && k == ks && uu == u) return true;
+          if (acc_of(tt + uu, NEX) == a) return false;
+        }
+  }
+  return true;
+}
 
 // slices of the left operand in processing order: descending, so that the
 // first MMAs of every k-block go to the inexact accumulator while the epilogue
@@ -419,15 +454,13 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
   } else if (warp == 1 && lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     constexpr uint32_t IDESC = idesc_bf16(BM, Cf::NT);
-    // bit a set: the next MMA into accumulator a starts it (enable_input_d = 0)
-    uint32_t fresh = (1u << Cf::NACC) - 1u;
     int a_iter = 0;
     bool ok = true;
-    // MMAs of slice t (all its pairs in `pass`: 0 all, 1 inexact levels, 2 exact levels), both K-steps.
-    // Per A plane and K-step, the MMAs over the right-operand slices u run back to back and share one A
-    // tile through the collector buffer (fill, use..., lastuse).  t and u are compile-time after
-    // unrolling, so levels, accumulators, descriptor offsets and collector hints fold.
-    auto issue_slice = [&](const int t, const int pass, const uint64_t adesc, const uint64_t bdesc) {
+    // MMAs of slice t (all its pairs in `pass`), both K-steps, in the order first_touch walks.  Per A plane
+    // and K-step, the MMAs over the right-operand slices u run back to back and share one A tile through the
+    // collector buffer (fill, use..., lastuse).  After unrolling, t, pass and mode are constants, so levels,
+    // accumulators, descriptor offsets, collector hints and enable flags all fold.
+    auto issue_slice = [&](const int t, const int pass, const int mode, const uint64_t adesc, const uint64_t bdesc) {
       int ulo = 0, uhi = Cf::MAXLEVEL - t;  // u range: levels t + ulo .. t + uhi
       if (pass == 1) ulo = NEX - t > 0 ? NEX - t : 0;
       if (pass == 2 && NEX - 1 - t < uhi) uhi = NEX - 1 - t;
@@ -443,20 +476,38 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
           for (int i = 0; i < S; ++i) {
             if (i >= cnt) continue;
             const int u = uhi - i;
-            const int level = t + u;
-            const int acc = level < NEX ? level : NEX;
+            const int acc = acc_of(t + u, NEX);
             const uint32_t dt = tmem + (uint32_t)(acc * Cf::NT);
             const uint64_t bslice = bdesc + (uint64_t)((u * Cf::B_SLICE) >> 4);
             // complex: [Cr | Ci] += Ar [Yr | Yi] (planes 1, 2) + Ai [-Yi | Yr] (planes 0, 1)
             const uint64_t b = (CPLX && pl == 0 ? bslice + (uint64_t)(Cf::B_PLANE >> 4) : bslice) + ko;
-            const uint32_t en = ((fresh >> acc) & 1u) ? 0u : 1u;
-            fresh &= ~(1u << acc);
-            if (cnt == 1) mma_bf16_c<0>(dt, a, b, IDESC, en);
-            else if (i == 0) mma_bf16_c<1>(dt, a, b, IDESC, en);
-            else if (i == cnt - 1) mma_bf16_c<3>(dt, a, b, IDESC, en);
-            else mma_bf16_c<2>(dt, a, b, IDESC, en);
+            const bool st = first_touch<S, NEX, Cf::AP>(t, pl, ks, u, pass, mode);
+            const int col = cnt == 1 ? 0 : (i == 0 ? 1 : (i == cnt - 1 ? 3 : 2));
+            if (st) {
+              if (col == 0) mma_bf16_ce<0, 0>(dt, a, b, IDESC);
+              else if (col == 1) mma_bf16_ce<1, 0>(dt, a, b, IDESC);
+              else if (col == 3) mma_bf16_ce<3, 0>(dt, a, b, IDESC);
+              else mma_bf16_ce<2, 0>(dt, a, b, IDESC);
+            } else {
+              if (col == 0) mma_bf16_ce<0, 1>(dt, a, b, IDESC);
+              else if (col == 1) mma_bf16_ce<1, 1>(dt, a, b, IDESC);
+              else if (col == 3) mma_bf16_ce<3, 1>(dt, a, b, IDESC);
+              else mma_bf16_ce<2, 1>(dt, a, b, IDESC);
+            }
           }
         }
+      }
+    };
+    // one pass over all slices (modes 0 and 2): slices in descending order, each slot released after its MMAs
+    auto one_pass = [&](const int mode, const uint64_t bdesc) {
+#pragma unroll
+      for (int ti = 0; ti < S; ++ti) {
+        const int as = (a_iter + ti) % Cf::A_SLOTS;
+        if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
+        if (!ok) break;
+        fence_after();
+        issue_slice(S - 1 - ti, 0, mode, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
+        mma_commit(smem_u32(&a_empty[as]));
       }
     };
     for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -468,19 +519,13 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
         break;
       }
       fence_after();
-      if (chunk_start) fresh |= (1u << NEX) - 1u;  // exact levels restart every chunk
       const uint64_t bdesc = sw64_desc(smem_u32(sB + bs * Cf::B_STAGE));
-      if (!(NEX > 0 && chunk_start && chunk > 0)) {
-        // one pass: slices in descending order, pairs of each slice inexact-first
-#pragma unroll
-        for (int ti = 0; ti < S; ++ti) {
-          const int as = (a_iter + ti) % Cf::A_SLOTS;
-          if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
-          if (!ok) break;
-          fence_after();
-          issue_slice(S - 1 - ti, 0, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
-          mma_commit(smem_u32(&a_empty[as]));
-        }
+      if (kb == 0) {
+        one_pass(0, bdesc);
+        if (!ok) break;
+        a_iter += S;
+      } else if (!(NEX > 0 && chunk_start)) {
+        one_pass(2, bdesc);
         if (!ok) break;
         a_iter += S;
       } else {
@@ -493,7 +538,7 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
           if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
           if (!ok) break;
           fence_after();
-          issue_slice(S - 1 - ti, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
+          issue_slice(S - 1 - ti, 1, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
           if (S - 1 - ti >= NEX) mma_commit(smem_u32(&a_empty[as]));
         }
         if (ok && !mbar_wait(smem_u32(tmem_empty), (chunk - 1) & 1, abort_sh, err)) ok = false;
@@ -503,7 +548,7 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
         for (int ti = 0; ti < S; ++ti) {
           if (S - 1 - ti >= NEX) continue;
           const int as = (a_iter + ti) % Cf::A_SLOTS;
-          issue_slice(S - 1 - ti, 2, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
+          issue_slice(S - 1 - ti, 2, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
           mma_commit(smem_u32(&a_empty[as]));
         }
         a_iter += S;
