@@ -119,6 +119,16 @@ void chase_set_wait_limit_ns(uint64_t ns);
  * Runs on its own stream of the current device and returns when it has finished. */
 chase_status chase_measure_fp64_peak(int which, double* tflops_out, double* ms_out);
 
+/* tcgen05 issue-rate probe (not part of Algorithm 1): cycles per MMA of the FP64 split-product kernel's
+ * per-k-block issue pattern (7 left slices, 28 digit pairs, 2 planes x 2 K-steps: 112 MMAs of M = 128,
+ * width n_cols, K = 16, bf16 operands, FP32 accumulators), issued back to back by one thread of one CTA per
+ * SM, zero operands.  variant 0: no synchronisation, n_cols in {16, 32, 64, 80, 96, 128, 256}; for n_cols = 80:
+ * variant bits 1 = a tcgen05.commit after each slice, 2 = a distinct left tile per slice, 4 = an mbarrier
+ * test (of a completed phase) before each slice, 8 = no A-collector hints (variants 1, 2, 3, 7, 8).  Cycles are
+ * clock64 counts of the issuing thread from the first MMA to the completion of the last, averaged over the
+ * SMs.  CHASE_ERR_UNSUPPORTED off sm_103; CHASE_ERR_ARG for other sizes or variants. */
+chase_status chase_measure_mma_issue(int n_cols, int variant, double* cycles_per_mma);
+
 /* Fill *opts with defaults. */
 void chase_default_opts(chase_opts* opts);
 

@@ -22,7 +22,8 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_NOCONV", 4: "ERR_QR_BREAK
 EXPORTED = ["chase_default_opts", "chase_create", "chase_destroy", "chase_last_error", "chase_workspace_bytes",
             "chase_solve", "chase_solve_batched", "chase_eigvals", "chase_eigvecs", "chase_stats", "chase_backward",
             "chase_kernel_launch_count", "chase_lanczos", "chase_filter", "chase_qr", "chase_rayleigh_ritz", "chase_heevj", "chase_heevj_noalloc", "chase_hemm",
-            "chase_generate", "chase_perturb", "chase_set_wait_limit_ns", "chase_measure_fp64_peak"]
+            "chase_generate", "chase_perturb", "chase_set_wait_limit_ns", "chase_measure_fp64_peak",
+            "chase_measure_mma_issue"]
 
 
 class Opts(C.Structure):
@@ -89,6 +90,7 @@ def load() -> C.CDLL:
         "chase_perturb": (I, [P, P, I64, I64, D, C.c_uint64]),
         "chase_set_wait_limit_ns": (None, [C.c_uint64]),
         "chase_measure_fp64_peak": (I, [I, C.POINTER(D), C.POINTER(D)]),
+        "chase_measure_mma_issue": (I, [I, I, C.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

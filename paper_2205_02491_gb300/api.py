@@ -211,6 +211,14 @@ def measure_fp64_peak(which: str = "dfma") -> float:
     return float(out.value)
 
 
+def measure_mma_issue(n_cols: int = 80, variant: int = 0) -> float:
+    """Cycles per tcgen05.mma of the split-product kernel's issue pattern (see chase_measure_mma_issue)."""
+    lib = L.load()
+    out = C.c_double()
+    L.check(None, lib.chase_measure_mma_issue(int(n_cols), int(variant), C.byref(out)))
+    return float(out.value)
+
+
 def set_wait_limit_ns(ns: int) -> None:
     """Testing hook: wall-clock limit of the Jacobi sweep kernel's grid-barrier waits (0: default 2 s)."""
     L.load().chase_set_wait_limit_ns(int(ns))

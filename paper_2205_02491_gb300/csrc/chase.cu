@@ -603,8 +603,13 @@ template <typename T> struct Solver {
     dbg_finite(G, k, k, k, sizeof(T), "G before the FP32 pass");
     convert_mat<T, F>(st(), k, G, k, Gf, k);
     try {
-      c->stats.rr_sweeps += heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40, false,
-                                           true);
+      // block Jacobi for quotients of a few blocks and more (its rounds scale with k / 32, not k); the scalar
+      // cooperative sweep below that
+      if (k >= 128 && jw_elems >= (int64_t)k * k + heev_block_workspace(k))
+        c->stats.rr_sweeps += heev_block_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40);
+      else
+        c->stats.rr_sweeps += heev_jacobi<F>(st(), k, Gf, k, w, Zf, k, jw, jw_elems, c->dwork, c->iwork, 3e-6, 40,
+                                             false, true);
     } catch (const Error& e) {
       // non-finite FP32 values: G itself is untouched and the FP64 solver takes over; a grid barrier
       // that hit its wait limit is reported as CHASE_ERR_TIMEOUT
@@ -620,7 +625,9 @@ template <typename T> struct Solver {
     const double scale = std::max(std::fabs(ends[0]), std::fabs(ends[1]));
     if (!(scale > 0.0) || !std::isfinite(scale)) return false;
     const double omega = 1e-5 * scale;
-    for (int it = 0; it < 3; ++it) {
+    // three first-order corrections: the FP32 pass stops at its rounding floor (up to about 1e-4 relative
+    // off-diagonal norm for large k), which quadratic convergence takes to FP64 level in three steps
+    for (int it = 0; it < 4; ++it) {
       if (!orthonormalize_small(Z, k, Gp, X)) return false;
       Epi e1;
       e1.C = Wk;
@@ -632,7 +639,7 @@ template <typename T> struct Solver {
       gemm(OP_C, Z, k, OP_N, Wk, k, k, k, k, e2, CHASE_FP64);  // G' = Z^H G Z
       hermitianize<T>(st(), k, Gp, k);
       dbg_finite(Gp, k, k, k, sizeof(T), "G' in the refinement");
-      if (it == 2) break;
+      if (it == 3) break;
       eig_correction<T>(st(), k, Gp, k, X, k, omega);
       Epi e3;
       e3.C = Wk;

@@ -9,6 +9,7 @@
 // the phase D = diag(1, conj(g)/|g|) and zeroed by the real rotation with
 // t = sign(z)/(|z| + sqrt(1+z^2)), z = (b-a)/(2|g|).
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -416,6 +417,307 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
   permute_cols<T>(st, k, k, Zu, k, Z, ldz, iwork);
   return sweeps;
 }
+
+// ---------------------------------------------------------------- block Jacobi (FP32 first pass)
+// Two-sided block Jacobi: the indices are cut into blocks of BJ_B; a round-robin tournament over the
+// blocks pairs them, and each round diagonalises every pair's 2 BJ_B x 2 BJ_B principal submatrix
+// S = G[IJ, IJ] in shared memory (cyclic Jacobi, one CTA per pair), then applies its unitary U to the
+// whole matrix: G[:, IJ] <- G[:, IJ] U and Z[:, IJ] <- Z[:, IJ] U, then G[IJ, :] <- U^H G[IJ, :].
+// A sweep has (blocks - 1) rounds instead of the scalar method's (k - 1), each doing dense
+// (k x 64) x (64 x 64) updates, so the round count (and its launch and synchronisation cost) falls by
+// the block width while the arithmetic per sweep stays 4 k^3 multiply-adds.
+constexpr int BJ_B = 32;          // block width
+constexpr int BJ_M = 2 * BJ_B;    // subproblem order
+constexpr int BJ_LD = BJ_M + 1;   // padded shared-memory row length
+constexpr int BJ_SOLVE_THREADS = 1024;
+constexpr int BJ_UPD_THREADS = 256;
+constexpr int BJ_TILE = 64;       // rows (columns) of G or Z per update CTA
+
+// global index of local index l of block pair (I, J)
+__device__ __forceinline__ int bj_global(int I, int J, int l) {
+  return l < BJ_B ? I * BJ_B + l : J * BJ_B + (l - BJ_B);
+}
+
+template <typename F>
+__global__ void __launch_bounds__(BJ_SOLVE_THREADS) bj_solve_kernel(int k, int nbp, int r, const F* G, int64_t ldg,
+                                                                     F* Ubuf, int max_inner, double tol_inner) {
+  using s = S<F>;
+  extern __shared__ __align__(16) unsigned char bj_smem[];
+  F* Sm = reinterpret_cast<F*>(bj_smem);  // S[l][m] at Sm[l * BJ_LD + m]
+  F* Um = Sm + BJ_M * BJ_LD;              // U[l][m] at Um[l * BJ_LD + m]
+  __shared__ int rp[BJ_M];
+  __shared__ F rself[BJ_M], rother[BJ_M];
+  __shared__ double red[2][BJ_SOLVE_THREADS / 32];
+  __shared__ int cont;
+  const int nb = (k + BJ_B - 1) / BJ_B;
+  int I, J;
+  round_pair(r, blockIdx.x, nbp, I, J);
+  if (I >= nb || J >= nb) return;  // paired with the padding block: nothing to do this round
+  const int tid = threadIdx.x;
+  for (int e = tid; e < BJ_M * BJ_M; e += blockDim.x) {
+    const int l = e % BJ_M, m = e / BJ_M;
+    const int gl = bj_global(I, J, l), gm = bj_global(I, J, m);
+    Sm[l * BJ_LD + m] = (gl < k && gm < k) ? G[gl + (int64_t)gm * ldg] : s::zero();
+    Um[l * BJ_LD + m] = (l == m) ? s::one() : s::zero();
+  }
+  __syncthreads();
+  for (int sw = 0; sw < max_inner; ++sw) {
+    // off-diagonal and total squared norms of S (block reduction)
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < BJ_M * BJ_M; e += blockDim.x) {
+      const int l = e % BJ_M, m = e / BJ_M;
+      const double a = s::abs2(Sm[l * BJ_LD + m]);
+      tot += a;
+      if (l != m) off += a;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = off;
+      red[1][tid >> 5] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+      cont = (a > tol_inner * tol_inner * b) && b > 0.0;
+    }
+    __syncthreads();
+    if (!cont) break;
+    for (int rr = 0; rr < BJ_M - 1; ++rr) {
+      if (tid < BJ_M / 2) {
+        int a, b;
+        round_pair(rr, tid, BJ_M, a, b);
+        const int p = min(a, b), q = max(a, b);
+        const bool valid = bj_global(I, J, q) < k && bj_global(I, J, p) < k;
+        const F g = Sm[p * BJ_LD + q];
+        const double ag = sqrt(s::abs2(g));
+        const double app = s::re(Sm[p * BJ_LD + p]), aqq = s::re(Sm[q * BJ_LD + q]);
+        if (!valid || !(ag > 1e-30)) {
+          rp[p] = q;
+          rself[p] = s::one();
+          rother[p] = s::zero();
+          rp[q] = p;
+          rself[q] = s::one();
+          rother[q] = s::zero();
+        } else {
+          const double z = (aqq - app) / (2.0 * ag);
+          const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
+          const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+          const F ph = s::scale(s::conj(g), 1.0 / ag);  // conj(g)/|g|
+          // J = [[c, sn], [-sn ph, c ph]] on (p, q): J[p][p], J[q][p] for p; J[q][q], J[p][q] for q
+          rp[p] = q;
+          rself[p] = s::make(c, 0.0);
+          rother[p] = s::scale(ph, -sn);
+          rp[q] = p;
+          rself[q] = s::scale(ph, c);
+          rother[q] = s::make(sn, 0.0);
+        }
+      }
+      __syncthreads();
+      // S <- J^H S J on every (row pair, column pair) 2x2 block, U <- U J; each item owns its entries
+      for (int it = tid; it < (BJ_M / 2) * (BJ_M / 2); it += blockDim.x) {
+        const int i1 = it % (BJ_M / 2), i2 = it / (BJ_M / 2);
+        int rows[2], cols[2];
+        round_pair(rr, i1, BJ_M, rows[0], rows[1]);
+        round_pair(rr, i2, BJ_M, cols[0], cols[1]);
+        F in[2][2], cu[2][2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) in[u][v] = Sm[rows[u] * BJ_LD + cols[v]];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v)
+            cu[u][v] = s::add(s::mul(in[u][v], rself[cols[v]]), s::mul(in[u][1 - v], rother[cols[v]]));
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            F o = s::add(s::mul(s::conj(rself[rows[u]]), cu[u][v]), s::mul(s::conj(rother[rows[u]]), cu[1 - u][v]));
+            if (rows[u] == cols[v]) o = s::make(s::re(o), 0.0);
+            if (i1 == i2 && u != v) o = s::zero();
+            Sm[rows[u] * BJ_LD + cols[v]] = o;
+          }
+      }
+      for (int it = tid; it < BJ_M * (BJ_M / 2); it += blockDim.x) {
+        const int i = it % BJ_M, pi = it / BJ_M;
+        int a, b;
+        round_pair(rr, pi, BJ_M, a, b);
+        const F ua = Um[i * BJ_LD + a], ub = Um[i * BJ_LD + b];
+        Um[i * BJ_LD + a] = s::add(s::mul(ua, rself[a]), s::mul(ub, rother[a]));
+        Um[i * BJ_LD + b] = s::add(s::mul(ub, rself[b]), s::mul(ua, rother[b]));
+      }
+      __syncthreads();
+    }
+  }
+  F* U = Ubuf + (int64_t)blockIdx.x * BJ_M * BJ_M;
+  for (int e = tid; e < BJ_M * BJ_M; e += blockDim.x) {
+    const int l = e % BJ_M, m = e / BJ_M;
+    U[l + m * BJ_M] = Um[l * BJ_LD + m];
+  }
+}
+
+// X[:, IJ] <- X[:, IJ] U for a tile of BJ_TILE rows (X = G for blockIdx.z == 0, Z for 1)
+template <typename F>
+__global__ void __launch_bounds__(BJ_UPD_THREADS) bj_cols_kernel(int k, int nbp, int r, F* G, int64_t ldg, F* Z,
+                                                                  int64_t ldz, const F* __restrict__ Ubuf) {
+  using s = S<F>;
+  extern __shared__ __align__(16) unsigned char bj_smem[];
+  F* Us = reinterpret_cast<F*>(bj_smem);   // BJ_M x BJ_LD
+  F* Xs = Us + BJ_M * BJ_LD;               // BJ_TILE x BJ_LD
+  const int nb = (k + BJ_B - 1) / BJ_B;
+  int I, J;
+  round_pair(r, blockIdx.y, nbp, I, J);
+  if (I >= nb || J >= nb) return;
+  F* X = blockIdx.z == 0 ? G : Z;
+  const int64_t ldx = blockIdx.z == 0 ? ldg : ldz;
+  const int r0 = blockIdx.x * BJ_TILE;
+  const F* U = Ubuf + (int64_t)blockIdx.y * BJ_M * BJ_M;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < BJ_M * BJ_M; e += blockDim.x) Us[(e % BJ_M) * BJ_LD + e / BJ_M] = U[e];
+  for (int e = tid; e < BJ_TILE * BJ_M; e += blockDim.x) {
+    const int i = e % BJ_TILE, l = e / BJ_TILE;
+    const int gi = r0 + i, gl = bj_global(I, J, l);
+    Xs[i * BJ_LD + l] = (gi < k && gl < k) ? X[gi + (int64_t)gl * ldx] : s::zero();
+  }
+  __syncthreads();
+  // thread: one row, BJ_M / 4 columns (c = cq + 4 j)
+  const int i = tid % BJ_TILE, cq = tid / BJ_TILE;
+  F acc[BJ_M / 4];
+#pragma unroll
+  for (int j = 0; j < BJ_M / 4; ++j) acc[j] = s::zero();
+  for (int m = 0; m < BJ_M; ++m) {
+    const F xv = Xs[i * BJ_LD + m];
+#pragma unroll
+    for (int j = 0; j < BJ_M / 4; ++j) acc[j] = s::fma(xv, Us[m * BJ_LD + cq + 4 * j], acc[j]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < BJ_M / 4; ++j) Xs[i * BJ_LD + cq + 4 * j] = acc[j];
+  __syncthreads();
+  for (int e = tid; e < BJ_TILE * BJ_M; e += blockDim.x) {
+    const int ii = e % BJ_TILE, l = e / BJ_TILE;
+    const int gi = r0 + ii, gl = bj_global(I, J, l);
+    if (gi < k && gl < k) X[gi + (int64_t)gl * ldx] = Xs[ii * BJ_LD + l];
+  }
+}
+
+// G[IJ, :] <- U^H G[IJ, :] for a tile of BJ_TILE columns
+template <typename F>
+__global__ void __launch_bounds__(BJ_UPD_THREADS) bj_rows_kernel(int k, int nbp, int r, F* G, int64_t ldg,
+                                                                  const F* __restrict__ Ubuf) {
+  using s = S<F>;
+  extern __shared__ __align__(16) unsigned char bj_smem[];
+  F* Us = reinterpret_cast<F*>(bj_smem);   // BJ_M x BJ_LD
+  F* Xs = Us + BJ_M * BJ_LD;               // Xs[l][j]: row l of the pair, column c0 + j (BJ_M x BJ_LD)
+  const int nb = (k + BJ_B - 1) / BJ_B;
+  int I, J;
+  round_pair(r, blockIdx.y, nbp, I, J);
+  if (I >= nb || J >= nb) return;
+  const int c0 = blockIdx.x * BJ_TILE;
+  const F* U = Ubuf + (int64_t)blockIdx.y * BJ_M * BJ_M;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < BJ_M * BJ_M; e += blockDim.x) Us[(e % BJ_M) * BJ_LD + e / BJ_M] = U[e];
+  for (int e = tid; e < BJ_M * BJ_TILE; e += blockDim.x) {
+    const int l = e % BJ_M, j = e / BJ_M;
+    const int gl = bj_global(I, J, l), gj = c0 + j;
+    Xs[l * BJ_LD + j] = (gl < k && gj < k) ? G[gl + (int64_t)gj * ldg] : s::zero();
+  }
+  __syncthreads();
+  // thread: one column j, BJ_M / 4 rows (l = lq + 4 q); out[l][j] = sum_m conj(U[m][l]) X[m][j]
+  const int j = tid % BJ_TILE, lq = tid / BJ_TILE;
+  F acc[BJ_M / 4];
+#pragma unroll
+  for (int q = 0; q < BJ_M / 4; ++q) acc[q] = s::zero();
+  for (int m = 0; m < BJ_M; ++m) {
+    const F xv = Xs[m * BJ_LD + j];
+#pragma unroll
+    for (int q = 0; q < BJ_M / 4; ++q) acc[q] = s::fma(s::conj(Us[m * BJ_LD + lq + 4 * q]), xv, acc[q]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < BJ_M / 4; ++q) Xs[(lq + 4 * q) * BJ_LD + j] = acc[q];
+  __syncthreads();
+  for (int e = tid; e < BJ_M * BJ_TILE; e += blockDim.x) {
+    const int l = e % BJ_M, jj = e / BJ_M;
+    const int gl = bj_global(I, J, l), gj = c0 + jj;
+    if (gl < k && gj < k) G[gl + (int64_t)gj * ldg] = Xs[l * BJ_LD + jj];
+  }
+}
+
+template <typename F> static size_t bj_smem_bytes() { return (size_t)2 * BJ_M * BJ_LD * sizeof(F); }
+
+int heev_block_workspace(int k) {
+  const int nb = (k + BJ_B - 1) / BJ_B;
+  const int nbp = nb + (nb & 1);
+  return nbp / 2 * BJ_M * BJ_M;
+}
+
+template <typename F>
+int heev_block_jacobi(cudaStream_t st, int k, F* G, int64_t ldg, double* w, F* Z, int64_t ldz, F* work,
+                      int64_t work_elems, double* dwork, int* iwork, double tol, int max_sweeps) {
+  const int nb = (k + BJ_B - 1) / BJ_B;
+  const int nbp = nb + (nb & 1);
+  const int npairs = nbp / 2;
+  CHASE_REQUIRE(k >= 1 && work_elems >= (int64_t)k * k + heev_block_workspace(k), 2,
+                "heev_block_jacobi: workspace too small");
+  F* Zu = work;
+  F* Ubuf = work + (int64_t)k * k;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, []() {
+    const int b = (int)bj_smem_bytes<F>();
+    attr = cudaFuncSetAttribute(bj_solve_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (attr == cudaSuccess) attr = cudaFuncSetAttribute(bj_cols_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (attr == cudaSuccess) attr = cudaFuncSetAttribute(bj_rows_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  });
+  CHASE_CUDA(attr);
+  set_identity_kernel<F><<<dim3(ceil_div(k, 256), k), 256, 0, st>>>(k, Zu, k);
+  CHASE_CHECK_LAUNCH();
+  double* part = dwork + 2;
+  double hstat[2];
+  double prev_off = 0.0;
+  int sweeps = 0;
+  const int tiles = ceil_div(k, BJ_TILE);
+  for (; sweeps <= max_sweeps; ++sweeps) {
+    offdiag_partial_kernel<F><<<k, 128, 0, st>>>(k, G, ldg, part);
+    CHASE_CHECK_LAUNCH();
+    offdiag_sum_kernel<<<1, 32, 0, st>>>(k, part, dwork);
+    CHASE_CHECK_LAUNCH();
+    CHASE_CUDA(cudaMemcpyAsync(hstat, dwork, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CHASE_CUDA(cudaStreamSynchronize(st));
+    CHASE_REQUIRE(isfinite(hstat[0]) && isfinite(hstat[1]), 5, "heev_block_jacobi: non-finite matrix");
+    if (sqrt(hstat[0]) <= tol * sqrt(hstat[1]) || k == 1 || sweeps == max_sweeps) break;
+    // FP32 floor: the 64-term updates leave off-diagonal rounding of about 8 eps_32 sqrt(k) relative, which can
+    // exceed tol for large k; once a sweep no longer quarters the off-diagonal norm below 1e-4 relative, the
+    // FP64 refinement that follows takes over
+    if (sweeps >= 2 && hstat[0] > 0.0625 * prev_off && sqrt(hstat[0]) <= 1e-4 * sqrt(hstat[1])) break;
+    prev_off = hstat[0];
+    for (int r = 0; r < nbp - 1; ++r) {
+      bj_solve_kernel<F><<<npairs, BJ_SOLVE_THREADS, bj_smem_bytes<F>(), st>>>(k, nbp, r, G, ldg, Ubuf, 1, 1e-6);
+      CHASE_CHECK_LAUNCH();
+      bj_cols_kernel<F><<<dim3(tiles, npairs, 2), BJ_UPD_THREADS, bj_smem_bytes<F>(), st>>>(k, nbp, r, G, ldg, Zu, k,
+                                                                                          Ubuf);
+      CHASE_CHECK_LAUNCH();
+      bj_rows_kernel<F><<<dim3(tiles, npairs), BJ_UPD_THREADS, bj_smem_bytes<F>(), st>>>(k, nbp, r, G, ldg, Ubuf);
+      CHASE_CHECK_LAUNCH();
+    }
+  }
+  diag_rank_kernel<F><<<ceil_div(k, 128), 128, 0, st>>>(k, G, ldg, w, iwork);
+  CHASE_CHECK_LAUNCH();
+  permute_cols<F>(st, k, k, Zu, k, Z, ldz, iwork);
+  return sweeps;
+}
+
+template int heev_block_jacobi<float>(cudaStream_t, int, float*, int64_t, double*, float*, int64_t, float*, int64_t,
+                                      double*, int*, double, int);
+template int heev_block_jacobi<float2>(cudaStream_t, int, float2*, int64_t, double*, float2*, int64_t, float2*,
+                                       int64_t, double*, int*, double, int);
 
 template int heev_jacobi<double>(cudaStream_t, int, double*, int64_t, double*, double*, int64_t, double*, int64_t,
                                  double*, int*, double, int, bool, bool);

@@ -4,7 +4,7 @@
 // the FP64 rate on GB300).  Its eigenvectors Z are then refined in FP64-class
 // arithmetic: with Z orthonormal and G' = Z^H G Z, the first-order correction
 // Z <- Z (I + X), X_pq = G'_pq / (d_q - d_p) for well separated d = diag(G'),
-// converges quadratically (two steps from FP32 accuracy reach FP64 accuracy).
+// converges quadratically (three steps take the FP32 pass, stopped at its rounding floor, to FP64 accuracy).
 // Pairs closer than omega (clusters) are left to an exact FP64 Jacobi on each
 // cluster's block of G', one block per cluster.
 #include "common.cuh"

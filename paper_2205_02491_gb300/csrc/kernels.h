@@ -69,6 +69,14 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
                 int64_t work_elems, double* dwork, int* iwork, double tol, int max_sweeps,
                 bool require_convergence = true, bool persistent = false);
 
+// Two-sided block Jacobi (blocks of 32, one CTA per block pair per round) for the FP32 first pass of the
+// mixed eigensolve: G (k x k, destroyed) -> w ascending, Z.  work: k*k + heev_block_workspace(k) scalars.
+// Returns the sweeps used (the cap is not an error: the FP64 refinement follows).
+int heev_block_workspace(int k);
+template <typename F>
+int heev_block_jacobi(cudaStream_t st, int k, F* G, int64_t ldg, double* w, F* Z, int64_t ldz, F* work,
+                      int64_t work_elems, double* dwork, int* iwork, double tol, int max_sweeps);
+
 // mixed-precision eigensolve helpers (eig_mixed.cu)
 template <typename T, typename F> void convert_mat(cudaStream_t st, int k, const T* in, int64_t ldi, F* out, int64_t ldo);
 template <typename T>

@@ -205,17 +205,19 @@ def test_solve_c1_all_split_products(pkg, mode):
     assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
 
 
-@pytest.mark.parametrize("cplx,k", [(True, 160), (False, 160), (True, 97)])
+@pytest.mark.parametrize("cplx,k", [(True, 160), (False, 160), (True, 97), (True, 300), (False, 300)])
 def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx, k):
-    # k >= 64 takes the FP32 Jacobi (one cooperative launch per sweep) + FP64-class refinement path;
-    # include exact eigenvalue clusters; odd k exercises the dummy index of the round-robin order
+    # k >= 64 takes the FP32 Jacobi + FP64-class refinement path (k >= 128: block Jacobi, blocks of 32 paired
+    # in a round-robin tournament; below: the scalar cooperative sweep); include exact eigenvalue clusters;
+    # odd k exercises the dummy index of the scalar round-robin order, k = 160 an odd block count (a padding
+    # block), k = 300 a partial last block
     n = 900
     g = np.random.default_rng(31)
     lam = np.sort(g.uniform(-1, 1, n))
     lam[10:13] = lam[10]          # a triple eigenvalue inside the projected window
     lam[40] = lam[41] + 1e-9       # a near-degenerate pair
     lam = np.sort(lam)
-    p = G.problem_small(n, 100, 60, complex_=cplx, lam=lam, seed_pid=31)
+    p = G.problem_small(n, 100, max(60, k - 100), complex_=cplx, lam=lam, seed_pid=31)
     A = p.dense()
     # a basis of (nearly) the lowest eigenvectors, mixed by a random unitary so that the quotient is
     # full; the 1e-7 perturbation moves Ritz values by ~1e-14, so the clusters survive in G
