@@ -73,6 +73,13 @@ template <int S, int NEX, bool CPLX, int NTT> struct Cfg {
   // holds 2 x 12 + 2 x B_STAGES + 3 mbarriers plus two words); narrow tiles, whose MMAs are short, need
   // the extra depth to keep the copies of the next k-block in flight
   static constexpr int A_SLOTS = A_FIT < 12 ? A_FIT : 12;
+  // Grouped synchronisation (the FP64 kernels whose ring holds exactly one k-block, slot = processing index):
+  // the first G0 slices in processing order (the smallest: 1 + 2 + 3 digit pairs for S = 7) travel with the
+  // right operand on its barrier and are released together, so a k-block costs 1 + (S - G0) barrier checks
+  // and 2 + (S - G0) commits instead of 1 + S and 1 + S.  Each barrier check of the issuing thread stalls the
+  // MMA queue (measured: about 170 cycles), so fewer checks keep the tensor pipe fed.
+  static constexpr bool GROUPED = (A_SLOTS == S) && (NEX > 0) && (S >= 6);
+  static constexpr int G0 = GROUPED ? 3 : 0;
   static constexpr int NACC = NEX + 1;
   static constexpr int TMEM_USED = NACC * NT;
   static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : (TMEM_USED <= 256 ? 256 : 512);
@@ -335,13 +342,27 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
         break;
       }
       ++b_issued;
-      mbar_expect_tx(smem_u32(&b_full[bs]), Cf::B_BYTES);
+      if (Cf::GROUPED) {
+        // the leading G0 slices' slots are released together (on a_empty[0]) and refilled with this k-block's
+        // right operand, all on b_full[bs]
+        if (!mbar_wait(smem_u32(&a_empty[0]), (kb & 1) ^ 1, abort_sh, err)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(smem_u32(&b_full[bs]), Cf::B_BYTES + Cf::G0 * Cf::A_SLOT);
+      } else {
+        mbar_expect_tx(smem_u32(&b_full[bs]), Cf::B_BYTES);
+      }
       // every slice and plane of the right operand's k-block in one copy (the box spans all S x BP planes,
       // landing plane-major exactly as the MMA descriptors expect)
       tma_load_3d(smem_u32(sB + bs * Cf::B_STAGE), &tmB, smem_u32(&b_full[bs]), k0, n0, 0);
       for (int ti = 0; ti < S; ++ti, ++a_iter) {
         const int t = S - 1 - ti;
         const int as = a_iter % Cf::A_SLOTS;
+        if (ti < Cf::G0) {  // grouped: slot as == ti, already free
+          tma_load_3d(smem_u32(sA + as * Cf::A_SLOT), &tmA, smem_u32(&b_full[bs]), k0, m0, t * Cf::AP);
+          continue;
+        }
         if (!mbar_wait(smem_u32(&a_empty[as]), ((a_iter / Cf::A_SLOTS) & 1) ^ 1, abort_sh, err)) {
           ok = false;
           break;
@@ -360,7 +381,7 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
         }
       }
     }
-    for (int i = 0; i < Cf::A_SLOTS; ++i) {
+    for (int i = Cf::G0; i < Cf::A_SLOTS; ++i) {
       int uses = a_iter / Cf::A_SLOTS + (i < a_iter % Cf::A_SLOTS ? 1 : 0);
       if (uses > 0) {
         unsigned long long t0 = globaltimer();
@@ -420,11 +441,14 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
 #pragma unroll
       for (int ti = 0; ti < S; ++ti) {
         const int as = (a_iter + ti) % Cf::A_SLOTS;
-        if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
-        if (!ok) break;
-        fence_after();
+        if (ti >= Cf::G0) {  // the grouped leading slices arrived with the right operand
+          if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
+          if (!ok) break;
+          fence_after();
+        }
         issue_slice(S - 1 - ti, 0, mode, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
-        mma_commit(smem_u32(&a_empty[as]));
+        if (ti >= Cf::G0) mma_commit(smem_u32(&a_empty[as]));
+        else if (ti == Cf::G0 - 1) mma_commit(smem_u32(&a_empty[0]));
       }
     };
     for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -452,11 +476,16 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
 #pragma unroll
         for (int ti = 0; ti < S; ++ti) {
           const int as = (a_iter + ti) % Cf::A_SLOTS;
-          if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
-          if (!ok) break;
-          fence_after();
+          if (ti >= Cf::G0) {
+            if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
+            if (!ok) break;
+            fence_after();
+          }
           issue_slice(S - 1 - ti, 1, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
-          if (S - 1 - ti >= NEX) mma_commit(smem_u32(&a_empty[as]));
+          if (S - 1 - ti >= NEX) {
+            if (ti >= Cf::G0) mma_commit(smem_u32(&a_empty[as]));
+            else if (ti == Cf::G0 - 1) mma_commit(smem_u32(&a_empty[0]));
+          }
         }
         if (ok && !mbar_wait(smem_u32(tmem_empty), (chunk - 1) & 1, abort_sh, err)) ok = false;
         if (!ok) break;
@@ -466,7 +495,8 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
           if (S - 1 - ti >= NEX) continue;
           const int as = (a_iter + ti) % Cf::A_SLOTS;
           issue_slice(S - 1 - ti, 2, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
-          mma_commit(smem_u32(&a_empty[as]));
+          if (ti >= Cf::G0) mma_commit(smem_u32(&a_empty[as]));
+          else if (ti == Cf::G0 - 1) mma_commit(smem_u32(&a_empty[0]));
         }
         a_iter += S;
       }
