@@ -80,6 +80,13 @@ template <int S, int NEX, bool CPLX, int NTT> struct Cfg {
   // MMA queue (measured: about 170 cycles), so fewer checks keep the tensor pipe fed.
   static constexpr bool GROUPED = (A_SLOTS == S) && (NEX > 0) && (S >= 6);
   static constexpr int G0 = GROUPED ? 3 : 0;
+  // The later slices go in groups too (processing indices {3, 4} and {5, ..., S-1}): a group's slots are
+  // loaded onto the barrier of its first slot and released together after its last slice.  A group's
+  // refill is issued when its slots are released and needed one k-block later, after at least the
+  // MMAs of the slices processed in between (60 or more), which covers the copy latency.  Without
+  // grouping every slice is its own group.
+  static constexpr int gfirst(int ti) { return !GROUPED ? ti : (ti < 3 ? 0 : (ti < 5 ? 3 : 5)); }
+  static constexpr int glast(int ti) { return !GROUPED ? ti : (ti < 3 ? 2 : (ti < 5 ? 4 : S - 1)); }
   static constexpr int NACC = NEX + 1;
   static constexpr int TMEM_USED = NACC * NT;
   static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : (TMEM_USED <= 256 ? 256 : 512);
@@ -363,13 +370,17 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
           tma_load_3d(smem_u32(sA + as * Cf::A_SLOT), &tmA, smem_u32(&b_full[bs]), k0, m0, t * Cf::AP);
           continue;
         }
-        if (!mbar_wait(smem_u32(&a_empty[as]), ((a_iter / Cf::A_SLOTS) & 1) ^ 1, abort_sh, err)) {
-          ok = false;
-          break;
+        // a group's first slice waits for the group's release and announces all of its bytes
+        const int fs = (a_iter - ti + Cf::gfirst(ti)) % Cf::A_SLOTS;  // slot of the group's first slice
+        if (ti == Cf::gfirst(ti)) {
+          if (!mbar_wait(smem_u32(&a_empty[as]), ((a_iter / Cf::A_SLOTS) & 1) ^ 1, abort_sh, err)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(smem_u32(&a_full[as]), (Cf::glast(ti) - ti + 1) * Cf::A_SLOT);
         }
-        mbar_expect_tx(smem_u32(&a_full[as]), Cf::A_SLOT);
         // both planes (re, im) of the slice in one copy
-        tma_load_3d(smem_u32(sA + as * Cf::A_SLOT), &tmA, smem_u32(&a_full[as]), k0, m0, t * Cf::AP);
+        tma_load_3d(smem_u32(sA + as * Cf::A_SLOT), &tmA, smem_u32(&a_full[fs]), k0, m0, t * Cf::AP);
       }
     }
     // drain: every issued copy must have landed before the CTA exits
@@ -382,6 +393,7 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
       }
     }
     for (int i = Cf::G0; i < Cf::A_SLOTS; ++i) {
+      if (Cf::GROUPED && i != Cf::gfirst(i)) continue;  // grouped: only a group's first slot has copies on it
       int uses = a_iter / Cf::A_SLOTS + (i < a_iter % Cf::A_SLOTS ? 1 : 0);
       if (uses > 0) {
         unsigned long long t0 = globaltimer();
@@ -441,13 +453,15 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
 #pragma unroll
       for (int ti = 0; ti < S; ++ti) {
         const int as = (a_iter + ti) % Cf::A_SLOTS;
-        if (ti >= Cf::G0) {  // the grouped leading slices arrived with the right operand
+        const int fs = (a_iter + Cf::gfirst(ti)) % Cf::A_SLOTS;
+        // the leading G0 slices arrived with the right operand; a later group is checked at its first slice
+        if (ti >= Cf::G0 && ti == Cf::gfirst(ti)) {
           if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
           if (!ok) break;
           fence_after();
         }
         issue_slice(S - 1 - ti, 0, mode, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
-        if (ti >= Cf::G0) mma_commit(smem_u32(&a_empty[as]));
+        if (ti >= Cf::G0 && ti == Cf::glast(ti)) mma_commit(smem_u32(&a_empty[fs]));
         else if (ti == Cf::G0 - 1) mma_commit(smem_u32(&a_empty[0]));
       }
     };
@@ -476,14 +490,16 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
 #pragma unroll
         for (int ti = 0; ti < S; ++ti) {
           const int as = (a_iter + ti) % Cf::A_SLOTS;
-          if (ti >= Cf::G0) {
+          const int fs = (a_iter + Cf::gfirst(ti)) % Cf::A_SLOTS;
+          if (ti >= Cf::G0 && ti == Cf::gfirst(ti)) {
             if (ok && !mbar_wait(smem_u32(&a_full[as]), ((a_iter + ti) / Cf::A_SLOTS) & 1, abort_sh, err)) ok = false;
             if (!ok) break;
             fence_after();
           }
           issue_slice(S - 1 - ti, 1, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
-          if (S - 1 - ti >= NEX) {
-            if (ti >= Cf::G0) mma_commit(smem_u32(&a_empty[as]));
+          // a group whose last slice has no exact pairs is done after this pass
+          if (S - 1 - Cf::glast(ti) >= NEX) {
+            if (ti >= Cf::G0 && ti == Cf::glast(ti)) mma_commit(smem_u32(&a_empty[fs]));
             else if (ti == Cf::G0 - 1) mma_commit(smem_u32(&a_empty[0]));
           }
         }
@@ -494,8 +510,9 @@ __global__ void __maxnreg__(168) oz_gemm_kernel(const __grid_constant__ GroupPar
         for (int ti = 0; ti < S; ++ti) {
           if (S - 1 - ti >= NEX) continue;
           const int as = (a_iter + ti) % Cf::A_SLOTS;
+          const int fs = (a_iter + Cf::gfirst(ti)) % Cf::A_SLOTS;
           issue_slice(S - 1 - ti, 2, 1, sw64_desc(smem_u32(sA + as * Cf::A_SLOT)), bdesc);
-          if (ti >= Cf::G0) mma_commit(smem_u32(&a_empty[as]));
+          if (ti >= Cf::G0 && ti == Cf::glast(ti)) mma_commit(smem_u32(&a_empty[fs]));
           else if (ti == Cf::G0 - 1) mma_commit(smem_u32(&a_empty[0]));
         }
         a_iter += S;
