@@ -165,7 +165,7 @@ class Clocks:
 # to the bench's n by (n / 8192)^2: at a fixed column count the launch has n / 128 row blocks, each streaming
 # planes of length n, so both the left- and the right-operand traffic grow as n^2.  Set to None when the
 # kernel changes until it is captured again.
-FILTER_TRAFFIC_N8192 = 25.147e9
+FILTER_TRAFFIC_N8192 = None
 
 
 def filter_traffic_bytes(n, ne, slices):
