@@ -161,11 +161,11 @@ class Clocks:
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one full-width filter launch of the
 # current kernel, captured at n = 8192 with 1600 columns (`bench.py --hemm-only fp64 --n 8192`, one launch,
-# --clock-control none; profiles/oz_gemm_fp64_complex_n8192.md): 24.387 GB read + 0.760 GB written.  Scaled
+# --clock-control none; profiles/oz_gemm_fp64_complex_n8192.md): 10.046 GB read + 0.235 GB written.  Scaled
 # to the bench's n by (n / 8192)^2: at a fixed column count the launch has n / 128 row blocks, each streaming
-# planes of length n, so both the left- and the right-operand traffic grow as n^2.  Set to None when the
-# kernel changes until it is captured again.
-FILTER_TRAFFIC_N8192 = None
+# planes of length n, so both the left- and the right-operand traffic grow as n^2.  Captures stay at n = 8192;
+# set to None when the kernel changes until it is captured again.
+FILTER_TRAFFIC_N8192 = 10.281e9
 
 
 def filter_traffic_bytes(n, ne, slices):

@@ -438,17 +438,31 @@ __device__ __forceinline__ int bj_global(int I, int J, int l) {
   return l < BJ_B ? I * BJ_B + l : J * BJ_B + (l - BJ_B);
 }
 
+// FP32 scalar helpers of the subproblem solver (GB300's FP64 units run about 64x slower than its FP32 ones,
+// and this is the FP32 pass: no double arithmetic in its inner loop)
+__device__ __forceinline__ float bj_abs2(float a) { return a * a; }
+__device__ __forceinline__ float bj_abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float bj_re(float a) { return a; }
+__device__ __forceinline__ float bj_re(float2 a) { return a.x; }
+__device__ __forceinline__ void bj_real(float& a) {}
+__device__ __forceinline__ void bj_real(float2& a) { a.y = 0.0f; }
+template <typename F> __device__ __forceinline__ F bj_real_scalar(float x);
+template <> __device__ __forceinline__ float bj_real_scalar<float>(float x) { return x; }
+template <> __device__ __forceinline__ float2 bj_real_scalar<float2>(float x) { return make_float2(x, 0.0f); }
+// conj(g) * s
+__device__ __forceinline__ float bj_conj_scaled(float g, float sc) { return g * sc; }
+__device__ __forceinline__ float2 bj_conj_scaled(float2 g, float sc) { return make_float2(g.x * sc, -g.y * sc); }
+__device__ __forceinline__ float bj_scaled(float g, float sc) { return g * sc; }
+__device__ __forceinline__ float2 bj_scaled(float2 g, float sc) { return make_float2(g.x * sc, g.y * sc); }
+
 template <typename F>
 __global__ void __launch_bounds__(BJ_SOLVE_THREADS) bj_solve_kernel(int k, int nbp, int r, const F* G, int64_t ldg,
-                                                                     F* Ubuf, int max_inner, double tol_inner) {
+                                                                     F* Ubuf, int inner_sweeps) {
   using s = S<F>;
   extern __shared__ __align__(16) unsigned char bj_smem[];
   F* Sm = reinterpret_cast<F*>(bj_smem);  // S[l][m] at Sm[l * BJ_LD + m]
   F* Um = Sm + BJ_M * BJ_LD;              // U[l][m] at Um[l * BJ_LD + m]
-  __shared__ int rp[BJ_M];
   __shared__ F rself[BJ_M], rother[BJ_M];
-  __shared__ double red[2][BJ_SOLVE_THREADS / 32];
-  __shared__ int cont;
   const int nb = (k + BJ_B - 1) / BJ_B;
   int I, J;
   round_pair(r, blockIdx.x, nbp, I, J);
@@ -461,32 +475,7 @@ __global__ void __launch_bounds__(BJ_SOLVE_THREADS) bj_solve_kernel(int k, int n
     Um[l * BJ_LD + m] = (l == m) ? s::one() : s::zero();
   }
   __syncthreads();
-  for (int sw = 0; sw < max_inner; ++sw) {
-    // off-diagonal and total squared norms of S (block reduction)
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < BJ_M * BJ_M; e += blockDim.x) {
-      const int l = e % BJ_M, m = e / BJ_M;
-      const double a = s::abs2(Sm[l * BJ_LD + m]);
-      tot += a;
-      if (l != m) off += a;
-    }
-    off = warp_sum(off);
-    tot = warp_sum(tot);
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = off;
-      red[1][tid >> 5] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        a += red[0][w];
-        b += red[1][w];
-      }
-      cont = (a > tol_inner * tol_inner * b) && b > 0.0;
-    }
-    __syncthreads();
-    if (!cont) break;
+  for (int sw = 0; sw < inner_sweeps; ++sw) {
     for (int rr = 0; rr < BJ_M - 1; ++rr) {
       if (tid < BJ_M / 2) {
         int a, b;
@@ -494,27 +483,25 @@ __global__ void __launch_bounds__(BJ_SOLVE_THREADS) bj_solve_kernel(int k, int n
         const int p = min(a, b), q = max(a, b);
         const bool valid = bj_global(I, J, q) < k && bj_global(I, J, p) < k;
         const F g = Sm[p * BJ_LD + q];
-        const double ag = sqrt(s::abs2(g));
-        const double app = s::re(Sm[p * BJ_LD + p]), aqq = s::re(Sm[q * BJ_LD + q]);
-        if (!valid || !(ag > 1e-30)) {
-          rp[p] = q;
+        const float ag = sqrtf(bj_abs2(g));
+        const float app = bj_re(Sm[p * BJ_LD + p]), aqq = bj_re(Sm[q * BJ_LD + q]);
+        if (!valid || !(ag > 1e-30f)) {
           rself[p] = s::one();
           rother[p] = s::zero();
-          rp[q] = p;
           rself[q] = s::one();
           rother[q] = s::zero();
         } else {
-          const double z = (aqq - app) / (2.0 * ag);
-          const double t = (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z));
-          const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
-          const F ph = s::scale(s::conj(g), 1.0 / ag);  // conj(g)/|g|
+          // t = sign(z) / (|z| + sqrt(1 + z^2)), z = (aqq - app) / (2 |g|); for |z| beyond FP32 range of z^2 the
+          // root is infinite and t = 0 (no rotation needed at that scale)
+          const float z = (aqq - app) / (2.0f * ag);
+          const float t = copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f)));
+          const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = t * c;
+          const F ph = bj_conj_scaled(g, 1.0f / ag);  // conj(g)/|g|
           // J = [[c, sn], [-sn ph, c ph]] on (p, q): J[p][p], J[q][p] for p; J[q][q], J[p][q] for q
-          rp[p] = q;
-          rself[p] = s::make(c, 0.0);
-          rother[p] = s::scale(ph, -sn);
-          rp[q] = p;
-          rself[q] = s::scale(ph, c);
-          rother[q] = s::make(sn, 0.0);
+          rself[p] = bj_real_scalar<F>(c);
+          rother[p] = bj_scaled(ph, -sn);
+          rself[q] = bj_scaled(ph, c);
+          rother[q] = bj_real_scalar<F>(sn);
         }
       }
       __syncthreads();
@@ -539,7 +526,7 @@ __global__ void __launch_bounds__(BJ_SOLVE_THREADS) bj_solve_kernel(int k, int n
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
             F o = s::add(s::mul(s::conj(rself[rows[u]]), cu[u][v]), s::mul(s::conj(rother[rows[u]]), cu[1 - u][v]));
-            if (rows[u] == cols[v]) o = s::make(s::re(o), 0.0);
+            if (rows[u] == cols[v]) bj_real(o);
             if (i1 == i2 && u != v) o = s::zero();
             Sm[rows[u] * BJ_LD + cols[v]] = o;
           }
@@ -699,7 +686,7 @@ int heev_block_jacobi(cudaStream_t st, int k, F* G, int64_t ldg, double* w, F* Z
     if (sweeps >= 2 && hstat[0] > 0.0625 * prev_off && sqrt(hstat[0]) <= 1e-4 * sqrt(hstat[1])) break;
     prev_off = hstat[0];
     for (int r = 0; r < nbp - 1; ++r) {
-      bj_solve_kernel<F><<<npairs, BJ_SOLVE_THREADS, bj_smem_bytes<F>(), st>>>(k, nbp, r, G, ldg, Ubuf, 1, 1e-6);
+      bj_solve_kernel<F><<<npairs, BJ_SOLVE_THREADS, bj_smem_bytes<F>(), st>>>(k, nbp, r, G, ldg, Ubuf, 1);
       CHASE_CHECK_LAUNCH();
       bj_cols_kernel<F><<<dim3(tiles, npairs, 2), BJ_UPD_THREADS, bj_smem_bytes<F>(), st>>>(k, nbp, r, G, ldg, Zu, k,
                                                                                           Ubuf);
