@@ -205,8 +205,9 @@ def test_solve_c1_all_split_products(pkg, mode):
     assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
 
 
-@pytest.mark.parametrize("cplx,k", [(True, 160), (False, 160), (True, 97), (True, 300), (False, 300)])
-def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx, k):
+@pytest.mark.parametrize("cplx,k,fine", [(True, 160, False), (False, 160, False), (True, 97, False),
+                                         (True, 300, False), (False, 300, False), (False, 300, True)])
+def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx, k, fine):
     # k >= 64 takes the FP32 Jacobi + FP64-class refinement path (k >= 128: block Jacobi, blocks of 32 paired
     # in a round-robin tournament; below: the scalar cooperative sweep); include exact eigenvalue clusters;
     # odd k exercises the dummy index of the scalar round-robin order, k = 160 an odd block count (a padding
@@ -216,6 +217,10 @@ def test_rayleigh_ritz_mixed_eigensolve(pkg, cplx, k):
     lam = np.sort(g.uniform(-1, 1, n))
     lam[10:13] = lam[10]          # a triple eigenvalue inside the projected window
     lam[40] = lam[41] + 1e-9       # a near-degenerate pair
+    if fine:
+        # a dense stretch: 250 eigenvalues 2e-4 apart (relative gaps like the Table 2 Geometric spectrum's),
+        # where the FP32 pass must stop well below the gaps for the FP64 corrections to converge
+        lam[50:300] = lam[50] + 2e-4 * np.arange(250)
     lam = np.sort(lam)
     p = G.problem_small(n, 100, max(60, k - 100), complex_=cplx, lam=lam, seed_pid=31)
     A = p.dense()
