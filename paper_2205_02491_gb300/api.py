@@ -70,20 +70,27 @@ class Chase:
 
     # ------------------------------------------------------------------ full solve
     def solve(self, At: torch.Tensor, nev: int, nex: int, tol: float, deg: int, mode="fp64",
-              V0t: torch.Tensor | None = None, L0t: torch.Tensor | None = None):
+              V0t: torch.Tensor | None = None, L0t: torch.Tensor | None = None, out=None):
         """At: column-major storage (n x n) of A; V0t: (ne x n) storage of V0; L0t: (runs x n).
 
         The inputs may be CUDA tensors or CPU tensors (pinned for DMA speed): the library copies host inputs
         to the device itself.  Returns (eigvals[nev] float64, eigvecs storage (nev x n), i.e. eigvecs =
-        result.mT), on At's device.
+        result.mT), on At's device, written into out = (w, Vt) when given (for host results, pinned buffers
+        the caller keeps avoid a pageable copy and a fresh allocation per call).
         """
         n = At.shape[-1]
         mode = L.MODES[mode] if isinstance(mode, str) else int(mode)
         self._chk(self.lib.chase_solve(self.ctx, _ptr(At), n, n, nev, nex, float(tol), int(deg), mode, _ptr(V0t),
                                        _ptr(L0t)))
         on_dev = 1 if At.is_cuda else 0
-        w = torch.empty(nev, dtype=torch.float64, device=At.device)
-        Vt = torch.empty((nev, n), dtype=self.dtype, device=At.device)
+        if out is not None:
+            w, Vt = out
+            if (w.shape != (nev,) or w.dtype != torch.float64 or Vt.shape != (nev, n) or Vt.dtype != self.dtype
+                    or w.is_cuda != At.is_cuda or Vt.is_cuda != At.is_cuda or not Vt.is_contiguous()):
+                raise ValueError("out must be (float64 [nev], contiguous [nev, n] of the solver dtype) on At's device")
+        else:
+            w = torch.empty(nev, dtype=torch.float64, device=At.device)
+            Vt = torch.empty((nev, n), dtype=self.dtype, device=At.device)
         self._chk(self.lib.chase_eigvals(self.ctx, _ptr(w), on_dev))
         self._chk(self.lib.chase_eigvecs(self.ctx, _ptr(Vt), n, on_dev))
         return w, Vt

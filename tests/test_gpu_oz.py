@@ -261,3 +261,10 @@ def test_solve_host_buffers_match_device(pkg, pinned):
     assert np.array_equal(w_h.numpy(), w_d.cpu().numpy())
     assert np.array_equal(V_h.numpy(), V_d.cpu().numpy())
     assert np.max(np.abs(w_h.numpy() - p.lam[:p.nev])) <= 1e-10 * p.norm2()
+    # caller-owned result buffers (out=): the same pairs, written in place
+    w_o = torch.empty(p.nev, dtype=torch.float64, pin_memory=pinned)
+    V_o = torch.empty((p.nev, p.n), dtype=torch.complex128, pin_memory=pinned)
+    r = s.solve(Ah, p.nev, p.nex, p.tol, p.deg, "fp64", V0h, L0h, out=(w_o, V_o))
+    assert r[0] is w_o and r[1] is V_o
+    assert np.array_equal(w_o.numpy(), w_d.cpu().numpy())
+    assert np.array_equal(V_o.numpy(), V_d.cpu().numpy())
