@@ -21,8 +21,8 @@
 //   Mixed modes (S = 2: 3 products, S = 3: 6 products): one FP32 accumulator.
 //
 // Complex operands use real tiles: with B1 = [Yr | Yi] and B2 = [-Yi | Yr]
-// (N = 2 x 64 columns) one accumulator of width 128 holds [Cr | Ci] =
-// Ar B1 + Ai B2.  A is the Hermitian matrix of the eigenproblem, whose K-major
+// (N = 2 x 40 columns in the FP64 modes, 2 x 64 or 2 x 128 in the mixed ones) one
+// accumulator holds [Cr | Ci] = Ar B1 + Ai B2.  A is the Hermitian matrix of the eigenproblem, whose K-major
 // rows are the conjugated columns of its column-major storage.
 //
 // Kernel roles (320 threads): warp 0 lane 0 issues TMA loads, warp 1 lane 0
@@ -30,6 +30,10 @@
 // quadrants, half of the accumulator columns each) run
 // the exact-level flushes and the fused FP64 epilogue
 //   C = alpha * acc + gamma * ycol[j] * Y + beta * Z.
+// The MMA issuer's barrier checks and commits stall its MMA queue (a check costs
+// about 200 cycles with the tensor pipe idle), so the FP64 kernels move the left
+// slices in three groups per k-block (Cfg::GROUPED): 3 checks and 4 commits per
+// 112 MMAs instead of one of each per slice.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA sets
 // an error flag, drains its copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -234,9 +238,6 @@ __host__ __device__ constexpr bool first_touch(int t, int pl, int ks, int u, int
   return true;
 }
 
-// slices of the left operand in processing order: descending, so that the
-// first MMAs of every k-block go to the inexact accumulator while the epilogue
-// flushes the exact ones
 // Parameters of one launch: G independent products (problems) C_p = L_p R_p, each with its own tensor maps,
 // sizes, scales and epilogue.  The launch's tiles are the problems' tiles back to back: problem p owns
 // blocks [tile_begin[p], tile_begin[p + 1]).  Passed as one __grid_constant__ parameter (the tensor maps
