@@ -311,6 +311,22 @@ def perturbation(n: int, seed: int, complex_: bool = True) -> np.ndarray:
     return s * H
 
 
+# Seeds of the start vectors the library draws when the caller passes none (CHASE_SEED_V0 / CHASE_SEED_L0 of
+# include/chase_gb300.h; a CPU test checks that the two agree).
+LIBRARY_SEED_V0 = 0x2205024910000001
+LIBRARY_SEED_L0 = 0x2205024910000002
+
+
+def library_start_vectors(n: int, m: int, seed: int, complex_: bool = True) -> np.ndarray:
+    """The n x m block the library draws for a null V0 (seed LIBRARY_SEED_V0, m = nev + nex) or a null L0
+    (seed LIBRARY_SEED_L0, m = Lanczos runs): element (i, j) is the counter-based normal of counter i + j n,
+    (x + i y)/sqrt(2) complex, x real."""
+    i = np.arange(n)[:, None]
+    j = np.arange(m)[None, :]
+    x, y = counter_normal_pairs(seed, (i + j * n).astype(np.uint64))
+    return (x + 1j * y) * np.sqrt(0.5) if complex_ else x
+
+
 def sequence_seed(pid: int, step: int) -> int:
     return (SEED_BASE + 4 * 1000 + pid) * 16 + step
 

@@ -147,9 +147,18 @@ const char* chase_last_error(const chase_ctx* ctx);
  * caller's) plus split-product buffers. */
 int64_t chase_workspace_bytes(int64_t n_max, int ne_max, chase_dtype dtype, const chase_opts* opts);
 
+/* Seeds of the start vectors the library draws when the caller passes none (chase_solve with V0 or L0
+ * NULL): element (i, j) of the n x m block is the counter-based normal of counter i + j n under the seed,
+ * SplitMix64 (Steele, Lea & Flood 2014) of seed ^ SplitMix64(2c) and of seed ^ SplitMix64(2c + 1) as two
+ * 53-bit uniforms u1 = (a >> 11 + 1) 2^-53, u2 = (b >> 11) 2^-53, Box-Muller r = sqrt(-2 ln u1), t = 2 pi u2;
+ * real: r cos t; complex: (r cos t + i r sin t) / sqrt(2).  A host program can reproduce the block. */
+#define CHASE_SEED_V0 0x2205024910000001ull
+#define CHASE_SEED_L0 0x2205024910000002ull
+
 /* Algorithm 1 end to end.  A: n x n Hermitian (lda >= n).  V0: n x (nev+nex)
- * start block (ld n); the caller supplies the random block (NULL is an error).
- * L0: n x lanczos_runs Lanczos start vectors (ld n).
+ * start block (ld n), or NULL: the library draws it (CHASE_SEED_V0 above; Algorithm 1 starts from a
+ * random block).  L0: n x lanczos_runs Lanczos start vectors (ld n), or NULL: drawn the same way
+ * (CHASE_SEED_L0).
  * A, V0 and L0 may be device pointers or host pointers (pinned or pageable):
  * host inputs are first copied to the device on the context's stream (pinned
  * memory is copied by DMA).  A host A needs a device copy of n x n elements,

@@ -674,6 +674,26 @@ template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda
   CHASE_CHECK_LAUNCH();
 }
 
+// Seeded start vectors: X[i + j ldx] = the counter-based normal of counter i + j rows ((x + i y)/sqrt(2) complex,
+// x real), the same generator as above.
+template <typename T>
+__global__ void fill_normal_kernel(T* X, int64_t rows, int64_t ldx, unsigned long long seed) {
+  using s = S<T>;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= rows) return;
+  const double2 g = normal_pair(seed, (unsigned long long)(i + j * rows));
+  X[i + j * ldx] = s::cplx ? s::make(0.7071067811865476 * g.x, 0.7071067811865476 * g.y) : s::make(g.x, 0.0);
+}
+
+template <typename T> void fill_normal(cudaStream_t st, T* X, int64_t rows, int cols, int64_t ldx, unsigned long long seed) {
+  if (rows <= 0 || cols <= 0) return;
+  CHASE_REQUIRE(cols <= 65535, 1, "fill_normal: too many columns");
+  dim3 grid(ceil_div(rows, 256), (unsigned)cols);
+  fill_normal_kernel<T><<<grid, 256, 0, st>>>(X, rows, ldx, seed);
+  CHASE_CHECK_LAUNCH();
+}
+
 // ============================================================== instantiations
 #define INST(T)                                                                                                   \
   template void gemm_f64<T>(cudaStream_t, Op, Op, int64_t, int64_t, int64_t, const T*, int64_t, const T*, int64_t, \
@@ -696,7 +716,8 @@ template <typename T> void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda
   template void generate_wy<T>(cudaStream_t, T*, int64_t, int64_t, const double*, const T*, const T*, const T*, int); \
   template void zero_upper<T>(cudaStream_t, int, T*, int64_t);                                                    \
   template void trtri_diag<T>(cudaStream_t, int, T*, int64_t);                                                   \
-  template void perturb<T>(cudaStream_t, T*, int64_t, int64_t, double, unsigned long long);
+  template void perturb<T>(cudaStream_t, T*, int64_t, int64_t, double, unsigned long long);                      \
+  template void fill_normal<T>(cudaStream_t, T*, int64_t, int, int64_t, unsigned long long);
 INST(double)
 INST(double2)
 #undef INST

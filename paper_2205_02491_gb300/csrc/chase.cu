@@ -1289,9 +1289,26 @@ static bool is_host_ptr(const void* p) {
 chase_status chase_solve(chase_ctx* c, const void* A, int64_t n, int64_t lda, int nev, int nex, double tol, int deg,
                          int mode, const void* V0, const void* L0) {
   API_BEGIN(c)
-  CHASE_REQUIRE(A && V0 && L0, CHASE_ERR_ARG, "null A, V0 or L0");
+  CHASE_REQUIRE(A, CHASE_ERR_ARG, "null A");
   CHASE_REQUIRE(n >= 1 && n <= c->n_max && lda >= n, CHASE_ERR_ARG, "n or lda out of range for this context");
   CHASE_REQUIRE(nev >= 1 && nex >= 0 && nev + nex <= c->ne_max, CHASE_ERR_ARG, "nev/nex out of range");
+  // start vectors the caller leaves to the library: seeded counter-based normals (see the header)
+  if (!V0) {
+    // the filter partner buffer is free until the first filter step (V0 is read before it)
+    if (c->dtype == CHASE_C128)
+      fill_normal<double2>(c->stream, (double2*)c->T1, n, nev + nex, n, CHASE_SEED_V0);
+    else
+      fill_normal<double>(c->stream, (double*)c->T1, n, nev + nex, n, CHASE_SEED_V0);
+    V0 = c->T1;
+  }
+  if (!L0) {
+    if (!c->l0_stage) CHASE_CUDA(cudaMalloc(&c->l0_stage, (size_t)c->n_max * 8 * c->esz));
+    if (c->dtype == CHASE_C128)
+      fill_normal<double2>(c->stream, (double2*)c->l0_stage, n, c->opts.lanczos_runs, n, CHASE_SEED_L0);
+    else
+      fill_normal<double>(c->stream, (double*)c->l0_stage, n, c->opts.lanczos_runs, n, CHASE_SEED_L0);
+    L0 = c->l0_stage;
+  }
   // host inputs: copied to the device on the context's stream (pinned memory: DMA at link speed)
   const size_t esz = c->esz;
   if (is_host_ptr(A)) {

@@ -105,6 +105,10 @@ void generate_wy(cudaStream_t st, T* A, int64_t n, int64_t lda, const double* la
 template <typename T>
 void perturb(cudaStream_t st, T* A, int64_t n, int64_t lda, double eps, unsigned long long seed);
 
+// X (rows x cols, ld ldx) <- seeded counter-based normals (SplitMix64 + Box-Muller; complex: (x + i y)/sqrt(2)),
+// counter i + j rows: the library's start block and Lanczos start vectors when the caller passes none
+template <typename T> void fill_normal(cudaStream_t st, T* X, int64_t rows, int cols, int64_t ldx, unsigned long long seed);
+
 // Bookkeeping (Algorithm 1, lines 8-14) on the device.  See chase.cu for the layout of `bk`.
 void bookkeeping(cudaStream_t st, int k, const double* ritz, const double* res, double thresh, double b_sup,
                  double* bounds, int maxdeg, int extra_deg, int* out_lock, int* out_deg, int* out_perm,

@@ -138,6 +138,26 @@ def test_solve_fp64_split_vs_oracle(pkg, cplx, n, nev, nex):
     assert abs(st["iterations"] - ref.iterations) <= 1
 
 
+def test_solve_with_library_start_vectors(pkg):
+    """chase_solve with V0 and L0 left to the library (null): it draws them with the header's seeded
+    generator, reaches the prescribed spectrum, and takes the iterations of the oracle run from the host
+    restatement of the same vectors (within one)."""
+    p = G.problem_c1()
+    A = p.dense()
+    s = pkg.Chase(p.n, p.ne, complex_=True)
+    w, Vt = s.solve(dev(A), p.nev, p.nex, p.tol, p.deg, "fp64")
+    w = w.cpu().numpy()
+    V = host(Vt)
+    nrm = p.norm2()
+    assert np.max(np.abs(w - p.lam[:p.nev])) <= 1e-10 * nrm
+    R = G.implicit_matvec(p.lam, p.U, V) - V * w[None, :]
+    assert np.max(np.linalg.norm(R, axis=0)) <= 1e-10 * nrm * 1.01
+    V0 = G.library_start_vectors(p.n, p.ne, G.LIBRARY_SEED_V0, True)
+    L0 = G.library_start_vectors(p.n, 4, G.LIBRARY_SEED_L0, True)
+    ref = O.chase_solve(A, p.nev, p.nex, p.tol, p.deg, p.maxdeg, V0, L0, p.lanczos_steps)
+    assert abs(s.stats()["iterations"] - ref.iterations) <= 1
+
+
 @pytest.mark.parametrize("mode", ["fp64", "bf16x3", "bf16x6"])
 def test_solve_c1_modes(pkg, mode):
     p = G.problem_c1()
