@@ -420,9 +420,10 @@ int heev_jacobi(cudaStream_t st, int k, T* G, int64_t ldg, double* w, T* Z, int6
 
 // ---------------------------------------------------------------- block Jacobi (FP32 first pass)
 // Two-sided block Jacobi: the indices are cut into blocks of BJ_B; a round-robin tournament over the
-// blocks pairs them, and each round diagonalises every pair's 2 BJ_B x 2 BJ_B principal submatrix
-// S = G[IJ, IJ] in shared memory (cyclic Jacobi, one CTA per pair), then applies its unitary U to the
-// whole matrix: G[:, IJ] <- G[:, IJ] U and Z[:, IJ] <- Z[:, IJ] U, then G[IJ, :] <- U^H G[IJ, :].
+// blocks pairs them, and each round reduces every pair's 2 BJ_B x 2 BJ_B principal submatrix
+// S = G[IJ, IJ] in shared memory (one sweep of parallel cyclic Jacobi, one CTA per pair, accumulating the
+// rotations in U), then applies U to the whole matrix: G[:, IJ] <- G[:, IJ] U and Z[:, IJ] <- Z[:, IJ] U,
+// then G[IJ, :] <- U^H G[IJ, :].
 // A sweep has (blocks - 1) rounds instead of the scalar method's (k - 1), each doing dense
 // (k x 64) x (64 x 64) updates, so the round count (and its launch and synchronisation cost) falls by
 // the block width while the arithmetic per sweep stays 4 k^3 multiply-adds.
